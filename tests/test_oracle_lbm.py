@@ -1,0 +1,251 @@
+"""Pins of the oracle's lattice-Boltzmann part against closed forms,
+conservation laws and textbook results (no GPU)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1411_2181_gb300 import synth
+
+CX = np.array([0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0])
+CY = np.array([0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1])
+CZ = np.array([0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1])
+
+
+def single_component(Lx, Ly, Lz, **kw):
+    p = dict(Lx=Lx, Ly=Ly, Lz=Lz, G=0.0, rho_in=1.0, rho_out=0.0)
+    p.update(kw)
+    rho = np.zeros((2, Lz, Ly, Lx))
+    rho[0] = 1.0
+    return p, rho
+
+
+def test_lattice_isotropy():
+    """D3Q19 weights: the moment identities used by the closed forms below
+    (sum w = 1, sum w c c = I/3, sum w c c c c = (dd+dd+dd)/9)."""
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    c = np.stack([CX, CY, CZ], 1).astype(float)
+    assert abs(w.sum() - 1) < 1e-15
+    assert np.allclose(np.einsum("i,ia,ib->ab", w, c, c), np.eye(3) / 3, atol=1e-15)
+    d = np.eye(3)
+    iso = (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d) + np.einsum("ad,bc->abcd", d, d)) / 9
+    assert np.allclose(np.einsum("i,ia,ib,ic,id->abcd", w, c, c, c, c), iso, atol=1e-15)
+
+
+def test_rest_state_is_fixed_point():
+    """Uniform densities at rest, C = I, still walls: nothing moves."""
+    p = dict(Lx=5, Ly=4, Lz=6, G=3.1, eta_M=0.3, visco_phase=1, eta_P=0.1, tau_P=50, L2=100,
+             rho_in=1.0, rho_out=0.04)
+    rho = np.empty((2, 6, 4, 5))
+    rho[0] = 0.7
+    rho[1] = 0.3
+    o = O.Oracle(p, rho)
+    f0, C0 = o.f.copy(), o.C.copy()
+    o.step(10)
+    assert np.abs(o.f - f0).max() < 1e-15
+    assert np.abs(o.C - C0).max() < 1e-15
+
+
+def test_exact_mass_conservation_with_moving_walls():
+    """Streaming + halfway bounce-back with moving walls + Guo source keep
+    each component's mass exactly (to rounding)."""
+    p = dict(Lx=16, Ly=12, Lz=10, G=3.1, Uw=0.05, eta_M=0.4, visco_phase=1, eta_P=0.15,
+             tau_P=30, L2=100, rho_in=1.0, rho_out=0.04)
+    rho = synth.droplet_densities(16, 12, 10, 3.5, seed=7, noise=1e-3)
+    o = O.Oracle(p, rho)
+    m0 = o.f.reshape(2, -1).sum(1)
+    o.step(60)
+    m1 = o.f.reshape(2, -1).sum(1)
+    assert np.all(np.abs(m1 - m0) / m0 < 1e-13)
+
+
+def test_couette_linear_profile():
+    """Walls moving at -Uw (z=-1/2) and +Uw (z=Lz-1/2): the steady profile is
+    u_x = Uw (2 (z+1/2)/W - 1), reproduced exactly by BGK + halfway BB."""
+    Lz, Uw = 16, 0.01
+    p, rho = single_component(4, 4, Lz, Uw=Uw, eta_M=0.5)
+    o = O.Oracle(p, rho)
+    o.step(1500)
+    u = o.detail()["u"]
+    z = np.arange(Lz)
+    exact = Uw * (2 * (z + 0.5) / Lz - 1)
+    assert np.abs(u[0, :, 1, 2] - exact).max() < 1e-12
+    assert np.abs(u[1:]).max() < 1e-14
+
+
+def test_poiseuille_exact_at_magic_tau():
+    """Body force g along x between still walls: u = g (z+1/2)(W-z-1/2)/(2 nu).
+    Exact for BGK + halfway bounce-back when (tau - 1/2)^2 = 3/16; a
+    first-order slip appears otherwise."""
+    Lz, g = 10, 1e-5
+    tau = 0.5 + np.sqrt(3.0) / 4
+    nu = (tau - 0.5) / 3
+    p, rho = single_component(2, 2, Lz, eta_M=nu, g=(g, 0, 0))
+    o = O.Oracle(p, rho)
+    o.step(4000)
+    u = o.detail()["u"][0, :, 0, 0]
+    z = np.arange(Lz)
+    exact = g / (2 * nu) * (z + 0.5) * (Lz - z - 0.5)
+    assert np.abs(u - exact).max() / exact.max() < 1e-10
+    # away from the magic value the same set-up shows the known slip error
+    p2, _ = single_component(2, 2, Lz, eta_M=1 / 6, g=(g, 0, 0))
+    o2 = O.Oracle(p2, rho)
+    o2.step(4000)
+    u2 = o2.detail()["u"][0, :, 0, 0]
+    exact2 = g / (2 / 6) * (z + 0.5) * (Lz - z - 0.5)
+    assert np.abs(u2 - exact2).max() / exact2.max() > 1e-3
+
+
+def _random_oracle(seed=3, shape=(6, 5, 4), **kw):
+    Lx, Ly, Lz = shape
+    p = dict(Lx=Lx, Ly=Ly, Lz=Lz, G=3.1, Uw=0.02, eta_M=0.35, visco_phase=2, eta_P=0.12,
+             tau_P=7.0, L2=60, rho_in=1.0, rho_out=0.04, g=(1e-4, -2e-4, 3e-4))
+    p.update(kw)
+    rho, vel, C = synth.random_state(Lx, Ly, Lz, seed)
+    o = O.Oracle(p)
+    # non-equilibrium populations: equilibrium at a random velocity plus noise
+    rng = np.random.default_rng(seed + 100)
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    for s in range(2):
+        cu = CX[:, None, None, None] * vel[0] + CY[:, None, None, None] * vel[1] + CZ[:, None, None, None] * vel[2]
+        uu = (vel ** 2).sum(0)
+        o.f[s] = w[:, None, None, None] * rho[s] * (1 + 3 * cu + 4.5 * cu ** 2 - 1.5 * uu)
+        o.f[s] *= 1 + rng.uniform(-0.02, 0.02, o.f[s].shape)
+    o.C[:] = C
+    return o
+
+
+def test_guo_moments_of_collision():
+    """Moments of the forced BGK collision (Guo et al. 2002): per component
+    sum f* = rho_s and sum c c f* = (1-w) Pi + w (rho_s/3 I + rho_s u u)
+    + (1 - w/2)(u F + F u); total momentum sum c f* = j + F; and the velocity
+    is u = (j + F/2)/rho."""
+    o = _random_oracle()
+    d = o.detail()
+    f, fp, rho, u, F = o.f, d["fpost"], d["rho"], d["u"], d["Ftot"]
+    c = np.stack([CX, CY, CZ]).astype(float)
+    der = o.derived()
+    rt = rho.sum(0)
+    tau = 3 * (rho[0] * der.nu_A + rho[1] * der.nu_B) / rt + 0.5
+    om = 1 / tau
+    jtot = np.einsum("ai,sizyx->azyx", c, f)
+    Ftot = F.sum(0)
+    assert np.allclose(fp.sum(1), f.sum(1), rtol=0, atol=1e-14)
+    assert np.allclose(rho, f.sum(1), atol=1e-14)
+    assert np.allclose(u * rt, jtot + 0.5 * Ftot, atol=1e-14)
+    assert np.allclose(np.einsum("ai,sizyx->azyx", c, fp), jtot + Ftot, atol=1e-14)
+    for s in range(2):
+        Pi = np.einsum("ai,bi,izyx->abzyx", c, c, f[s])
+        Pis = np.einsum("ai,bi,izyx->abzyx", c, c, fp[s])
+        eq = rho[s] * (np.eye(3)[:, :, None, None, None] / 3 + np.einsum("azyx,bzyx->abzyx", u, u))
+        uF = np.einsum("azyx,bzyx->abzyx", u, F[s])
+        expect = (1 - om) * Pi + om * eq + (1 - om / 2) * (uF + uF.transpose(1, 0, 2, 3, 4))
+        assert np.allclose(Pis, expect, atol=1e-13)
+
+
+def test_shan_chen_force_closed_form():
+    """rho_B = a + b cos(k x), rho_A uniform: the D3Q19 sum gives
+    F_A,x = G rho_A b sin(k) sin(k x)/3 exactly (all planes with c_x = 1 carry
+    total weight 1/6) and no y, z component."""
+    Lx, Ly, Lz = 12, 3, 4
+    G, a, b = 3.1, 0.5, 0.2
+    k = 2 * np.pi / Lx
+    x = np.arange(Lx)
+    rho = np.empty((2, Lz, Ly, Lx))
+    rho[0] = 0.8
+    rho[1] = a + b * np.cos(k * x)
+    F = O.sc_force(dict(Lx=Lx, Ly=Ly, Lz=Lz, G=G, eta_M=0.3), rho)
+    exact = G * 0.8 * b * np.sin(k) * np.sin(k * x) / 3
+    assert np.abs(F[0, 0] - exact).max() < 1e-14
+    assert np.abs(F[0, 1:]).max() < 1e-14
+    # the force on B pushes B down the gradient of A: uniform A -> none
+    assert np.abs(F[1]).max() < 1e-14
+
+
+def test_shan_chen_momentum_balance():
+    """Newton's third law of the pair force: the tangential components of the
+    total Shan-Chen force vanish over the box (walls only take z momentum)."""
+    rho, _, _ = synth.random_state(7, 6, 5, seed=11)
+    F = O.sc_force(dict(Lx=7, Ly=6, Lz=5, G=3.1, eta_M=0.3), rho)
+    tot = F.sum(axis=(0, 2, 3, 4))
+    assert abs(tot[0]) < 1e-12 and abs(tot[1]) < 1e-12
+
+
+def test_polymer_force_closed_form():
+    """C = I + c(y) (e_x e_y + e_y e_x), c = b sin(k y): tr C = 3 so f = 1 and
+    Pi_xy = (eta_P/tau_P) chi b sin(k y); the central difference gives
+    F_P,x = (eta_P/tau_P) chi b sin(k) cos(k y), F_P,y = F_P,z = 0."""
+    Lx, Ly, Lz = 3, 10, 4
+    k = 2 * np.pi / Ly
+    b, etaP, tauP = 0.3, 0.4, 8.0
+    y = np.arange(Ly)
+    rho = np.empty((2, Lz, Ly, Lx))
+    rho[0] = 0.9
+    rho[1] = 0.1
+    C = np.zeros((6, Lz, Ly, Lx))
+    C[0] = C[1] = C[2] = 1
+    C[3] = (b * np.sin(k * y))[None, :, None]
+    p = dict(Lx=Lx, Ly=Ly, Lz=Lz, eta_M=1.0, visco_phase=1, eta_P=etaP, tau_P=tauP, L2=100, G=0)
+    FP = O.polymer_force(p, rho, C)
+    chi = 0.9 / 1.0
+    exact = etaP / tauP * chi * b * np.sin(k) * np.cos(k * y)
+    assert np.abs(FP[0] - exact[None, :, None]).max() < 1e-15
+    assert np.abs(FP[1:]).max() < 1e-15
+    # matrix viscoelasticity weights the same stress by rho_B/rho
+    p["visco_phase"] = 2
+    FP2 = O.polymer_force(p, rho, C)
+    assert np.abs(FP2[0] - exact[None, :, None] * (0.1 / 0.9)).max() < 1e-15
+
+
+def test_viscosity_split_gives_unit_total_ratio():
+    """Sec. 2: with lambda = 1 the total (solvent + polymer) viscosity of the
+    viscoelastic phase equals the Newtonian phase's; with the composition
+    weights used here this holds exactly in both bulk phases."""
+    for phase in (1, 2):
+        p = dict(Lx=2, Ly=2, Lz=2, eta_M=0.9, visco_phase=phase, eta_P=0.36, tau_P=10,
+                 rho_in=1.0, rho_out=0.04)
+        d = O.Oracle(p).derived()
+        for rA, rB in ((1.0, 0.04), (0.04, 1.0)):
+            rt = rA + rB
+            solvent = rt * (rA * d.nu_A + rB * d.nu_B) / rt
+            chi = (rA if phase == 1 else rB) / rt
+            assert abs(solvent + d.pi_coef * 10 * chi - 0.9) < 1e-14
+
+
+def test_flat_interface_coexistence():
+    """Two-component Shan-Chen with psi = rho: a flat interface separates
+    bulk phases that obey, to the accuracy of the gradient expansion,
+    ln(rho_maj/rho_min) = G (rho_maj - rho_min) (equal chemical potentials
+    of mu_s = ln rho_s + G rho_t)."""
+    L, G = 48, 3.1
+    p = dict(Lx=L, Ly=1, Lz=4, Uw=0.0, G=G, eta_M=1.04 / 6, rho_in=1.0, rho_out=0.04)
+    o = O.Oracle(p, synth.slab_densities(L, 1, 4, 24))
+    o.step(3000)
+    r = o.detail()["rho"][:, 1, 0, :]
+    a, b = r[0, L // 2], r[1, L // 2]
+    assert abs(np.log(a / b) / (G * (a - b)) - 1) < 0.05
+    # symmetric phases
+    assert abs(r[0, 2] - b) < 1e-4 and abs(r[1, 2] - a) < 1e-4
+
+
+def test_laplace_law_cylinder():
+    """Static cylindrical droplet: p_in - p_out = sigma/R with
+    p = (rho_A + rho_B)/3 + G rho_A rho_B/3; linear in 1/R through ~0."""
+    L, G = 48, 3.1
+    res = []
+    for R in (8, 11, 14):
+        p = dict(Lx=L, Ly=1, Lz=L, Uw=0.0, G=G, eta_M=1.04 / 6, rho_in=1.0, rho_out=0.04)
+        o = O.Oracle(p, synth.cylinder_densities(L, 1, L, R))
+        o.step(3000)
+        r = o.detail()["rho"]
+        P = (r[0] + r[1]) / 3 + G / 3 * r[0] * r[1]
+        c = L // 2
+        res.append((R, P[c, 0, c] - P[c, 0, 2]))
+    R = np.array([a for a, _ in res], float)
+    dp = np.array([b for _, b in res])
+    A = np.vstack([1 / R, np.ones_like(R)]).T
+    (sigma, icpt), *_ = np.linalg.lstsq(A, dp, rcond=None)
+    pred = A @ [sigma, icpt]
+    r2 = 1 - ((dp - pred) ** 2).sum() / ((dp - dp.mean()) ** 2).sum()
+    assert sigma > 0
+    assert r2 > 0.999
+    assert abs(icpt) < 0.15 * dp.max()
