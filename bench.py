@@ -1,0 +1,336 @@
+#!/usr/bin/env python
+"""Throughput of the hybrid LBM / FENE-P time step on one GB300.
+
+Workload (default): the weakly confined matrix-viscoelastic droplet,
+192 x 96 x 80 lattice (W = 80, R = 16, 2R/W = 0.4, lambda = 1, De = 1,
+L^2 = 100, eta_P/eta_M = 0.4, Ca = 0.2), FP32.  One bench step is one
+lattice time step over the whole box (every population and conformation
+component read and written once).  The state (about 0.6 GB) is larger than
+the 129 MB L2, so no flush is needed between steps.
+
+Printed JSON line: MLUPS (whole job), roofline of the step kernels against
+the measured HBM bandwidth, the end-to-end MLUPS through the C ABI with the
+initial densities copied from pinned host memory and the observables read
+back inside the timed region, the FP64 CPU oracle timed on the host cores,
+clocks sampled during the timed region and the kernel-launch count.
+
+``--impl reference`` times the CPU oracle itself (the reference arm of this
+method, which has no other implementation) on a bounded sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ALGO_BYTES = {0: 352, 1: 200, 2: 200}   # per lattice update: 2x19 populations + 6 C, read + write
+DTYPE = {0: "f32", 1: "f16-store/f32", 2: "bf16-store/f32"}
+METRIC = "MLUPS"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="matrix_ve_192x96x80",
+                    choices=["matrix_ve_192x96x80", "droplet_ve_256x128x64", "box_32cubed"])
+    ap.add_argument("--precision", choices=["fp32", "fp16", "bf16"], default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name: str, precision: int):
+    from dataclasses import replace
+    from paper_1411_2181_gb300 import configs
+    if name == "matrix_ve_192x96x80":
+        p, rho, _ = configs.config2(0.2)
+    elif name == "droplet_ve_256x128x64":
+        p, rho, _ = configs.config3()
+    else:
+        p, rho, _ = configs.config1()
+    return replace(p, precision=precision), rho
+
+
+def config_dict(name, p):
+    return {"workload": name, "lattice": [p.Lx, p.Ly, p.Lz], "cells": p.N, "W": p.Lz, "R": p.R,
+            "visco_phase": ["newtonian", "droplet", "matrix"][p.visco_phase], "lambda": p.lambda_,
+            "L2": p.L2, "Uw": p.Uw, "l2_policy": "state (>0.5 GB) larger than L2; no flush"}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- roofline inputs
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for fn in sorted(os.listdir(os.path.join(ROOT, "paper_1411_2181_gb300", "csrc"))):
+        if fn.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(ROOT, "paper_1411_2181_gb300", "csrc", fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload_name: str, precision: int):
+    """DRAM bytes per lattice update of the step from the committed ncu
+    summary, if it was taken on the current kernel sources."""
+    fn = os.path.join(ROOT, "profiles", f"step_{workload_name}_{['fp32', 'fp16', 'bf16'][precision]}.md")
+    if not os.path.exists(fn):
+        return None, None
+    txt = open(fn).read()
+    m_h = re.search(r"kernel source hash:\s*`?([0-9a-f]{16})", txt)
+    m_b = re.search(r"dram bytes per lattice update:\s*([0-9.]+)", txt)
+    if not m_h or not m_b or m_h.group(1) != kernel_source_hash():
+        return None, fn
+    return float(m_b.group(1)), fn
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_sample(p, rho, budget_s=12.0, max_steps=None):
+    """Time the FP64 oracle (as it stands) on a z-slab of the workload box:
+    the full x-y plane, depth chosen so one step takes about 1 s."""
+    import numpy as np
+    from oracle import oracle as O
+    O.build()
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    d = p.oracle_dict()
+    # probe a thin slab to estimate the rate, then size the sample
+    dz = max(4, min(p.Lz, 8))
+    d2 = dict(d, Lz=dz)
+    o = O.Oracle(d2, np.ascontiguousarray(rho[:, :dz]))
+    t = time.perf_counter(); o.step(1); rate = p.Lx * p.Ly * dz / (time.perf_counter() - t)
+    dz = int(max(4, min(p.Lz, rate * 1.0 / (p.Lx * p.Ly))))
+    steps = int(max(2, min(max_steps or 10 ** 9, budget_s * rate / (p.Lx * p.Ly * dz))))
+    d3 = dict(d, Lz=dz)
+    o = O.Oracle(d3, np.ascontiguousarray(rho[:, :dz]))
+    t = time.perf_counter(); o.step(steps); dt = time.perf_counter() - t
+    mlups = p.Lx * p.Ly * dz * steps / dt / 1e6
+    return {"value": round(mlups, 4), "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} FP64 oracle steps on a {p.Lx}x{p.Ly}x{dz} slab of the workload "
+                      f"(walls at both ends), {dt:.1f} s, OpenMP threads={cores}"}
+
+
+# ---------------------------------------------------------------- ours
+def run_ours(a):
+    import numpy as np
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1411_2181_gb300 import build
+    if rank == 0 or not dist:
+        build.build()
+    if dist:
+        tdist.barrier()
+    from paper_1411_2181_gb300 import lbfe
+    prec = {"fp32": 0, "fp16": 1, "bf16": 2}[a.precision]
+    p, rho = workload(a.workload, prec)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = lbfe.Solver(p, device=f"cuda:{local}", stream=stream)
+        s.init(0, rho)
+        for _ in range(a.warmup):
+            s.step(1)
+        torch.cuda.synchronize()
+        if dist:
+            tdist.barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            ev0.record(stream)
+            for _ in range(a.steps):
+                s.step(1)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        if dist:
+            tdist.barrier()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        st = s.check()
+    t_max = ms
+    if dist:
+        tt = torch.tensor([ms], device=f"cuda:{local}")
+        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    ms_per_step = t_max / a.steps
+    mlups_rank = p.N * a.steps / (t_max / 1e3) / 1e6
+    value = mlups_rank * world
+
+    # end to end through the C ABI: H2D of the initial densities from pinned
+    # memory, the steps, and the observables read back, all timed
+    e2e = None
+    if not a.no_e2e:
+        host = torch.from_numpy(np.ascontiguousarray(rho, dtype=np.float64)).pin_memory()
+        with torch.cuda.stream(stream):
+            s2 = lbfe.Solver(p, device=f"cuda:{local}", stream=stream)
+            s2.init_from_host_ptr(0, host.data_ptr())
+            s2.step(2)
+            s2.observables(0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s2.init_from_host_ptr(0, host.data_ptr())
+            s2.step(a.steps)
+            ob = s2.observables(0)
+            t1 = time.perf_counter()
+        e2e_mlups = p.N * a.steps / (t1 - t0) / 1e6 * world
+        obs_bytes = 6 * p.Lx * 8 + 2 * 8 + 4
+        e2e = {"value": round(e2e_mlups, 2), "unit": METRIC,
+               "h2d_bytes_per_step": int(host.numel() * 8 / a.steps),
+               "d2h_bytes_per_step": int(obs_bytes / a.steps),
+               "timed": "lbfe_init (pinned H2D of rho[2][N] float64) + lbfe_step(K) + lbfe_observables"}
+        del s2
+
+    peak, peak_kind = measured_peak()
+    algo = ALGO_BYTES[prec]
+    achieved = algo * p.N / (ms_per_step / 1e3) / 1e9
+    traffic_per_lup, prof_file = profiled_traffic(a.workload, prec)
+    roof = {"bound": "hbm", "kernel": "step (moments + forces + update kernels)",
+            "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "algorithmic_bytes_per_lup": algo,
+            "traffic": (round(traffic_per_lup * p.N) if traffic_per_lup else None),
+            "traffic_source": os.path.relpath(prof_file, ROOT) if (prof_file and traffic_per_lup) else None}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = oracle_sample(p, rho)
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": round(value, 2), "unit": METRIC, "n_gpus": world,
+               "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms_per_step, 5),
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": DTYPE[prec], "data": "synthetic (seeded droplet, NumPy PCG64)",
+               "config": config_dict(a.workload, p), "roofline": roof, "cpu_baseline": cpu,
+               "e2e": e2e, "clocks": clk.summary(), "gpu_launches": s.launches_per_step() * a.steps,
+               "status": lbfe._lib.lbfe_status_str(st).decode(),
+               "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+        print(json.dumps(out))
+    if dist:
+        tdist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import oracle as O
+    O.build()
+    prec = {"fp32": 0, "fp16": 1, "bf16": 2}[a.precision]
+    from paper_1411_2181_gb300 import configs
+    p, rho = workload(a.workload, prec)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    d = p.oracle_dict()
+    # each timed step: one oracle step on a z-slab of the box, sized so the
+    # whole run stays within about two minutes
+    probe = O.Oracle(dict(d, Lz=4), np.ascontiguousarray(rho[:, :4]))
+    t = time.perf_counter(); probe.step(1); rate = p.Lx * p.Ly * 4 / (time.perf_counter() - t)
+    per_step_s = 100.0 / max(1, a.steps + a.warmup)
+    dz = int(max(2, min(p.Lz, rate * per_step_s / (p.Lx * p.Ly))))
+    o = O.Oracle(dict(d, Lz=dz), np.ascontiguousarray(rho[:, :dz]))
+    for _ in range(a.warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        o.step(1)
+    dt = time.perf_counter() - t0
+    mlups = p.Lx * p.Ly * dz * a.steps / dt / 1e6
+    sample = f"one FP64 oracle step per bench step on a {p.Lx}x{p.Ly}x{dz} slab of the workload"
+    out = {"impl": "reference", "metric": METRIC, "value": round(mlups, 4), "unit": METRIC, "n_gpus": a.gpus,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(dt / a.steps * 1e3, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded droplet, NumPy PCG64)", "config": config_dict(a.workload, p),
+           "cpu_baseline": {"value": round(mlups, 4), "unit": METRIC, "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(mlups, 4), "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)

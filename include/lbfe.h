@@ -1,0 +1,190 @@
+/*
+ * lbfe.h -- C ABI of the GB300 hybrid lattice-Boltzmann / FENE-P droplet
+ * solver (Gupta & Sbragaglia, "Deformation and break-up of viscoelastic
+ * droplets using Lattice Boltzmann Models").
+ *
+ * The problem (Sec. 3, set-up; Fig. 1 sketch): a droplet of component A
+ * with radius R between two walls at gap W = Lz moving at -Uw (bottom,
+ * z = -1/2) and +Uw (top, z = Lz - 1/2) along x, periodic in x and y, in a
+ * matrix of component B.  Immiscibility is Shan-Chen (Sec. 2); the
+ * total-viscosity ratio is lambda (Sec. 2); one phase may carry FENE-P
+ * polymers (Eqs. 1-4) with viscosity eta_P, relaxation time tau_P and
+ * extensibility L^2 (Sec. 2).  The observables are deformation, orientation,
+ * projected length, neck count and break-up (Secs. 1 and 3, Figs. 2-4).
+ *
+ * Memory: the caller owns every buffer.  Device memory is one block the
+ * caller allocates (any CUDA allocator, e.g. PyTorch's) of at least the size
+ * lbfe_required_bytes() reports, 256-byte aligned, and keeps alive until
+ * lbfe_destroy(); the library carves its fields out of it and allocates no
+ * device memory of its own.  Host pointers are read or written only during
+ * the call that receives them.  All device work is enqueued on the CUDA
+ * stream given at creation (NULL = legacy default stream); calls that
+ * return host data synchronise that stream.
+ *
+ * Errors: every call returns an lbfe_status and never aborts, traps or
+ * exits.  A numerical blow-up (non-positive or NaN density, tr C >= L^2) is
+ * flagged on the device by the step kernels and reported as
+ * LBFE_ERR_DIVERGED by the next lbfe_observables() / lbfe_check().
+ *
+ * Field layout (the interface format of lbfe_get_field / lbfe_set_field):
+ *   cell index n = (z*Ly + y)*Lx + x, N = Lx*Ly*Lz;
+ *   populations f[(s*19 + i)*N + n], s = 0 (A, droplet), 1 (B, matrix);
+ *   D3Q19 order i: 0 rest; 1..6 = +x,-x,+y,-y,+z,-z;
+ *   7..18 = (1,1,0),(-1,-1,0),(1,-1,0),(-1,1,0),(1,0,1),(-1,0,-1),
+ *           (1,0,-1),(-1,0,1),(0,1,1),(0,-1,-1),(0,1,-1),(0,-1,1);
+ *   conformation C[k*N + n], k = xx, yy, zz, xy, xz, yz.
+ * The populations are the post-streaming (pre-collision) state.
+ */
+#ifndef LBFE_H
+#define LBFE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBFE_OK = 0,
+    LBFE_ERR_BAD_PARAM = 1,   /* invalid argument or parameter set (nothing enqueued) */
+    LBFE_ERR_NO_MEMORY = 2,   /* the device block given is smaller than required */
+    LBFE_ERR_CUDA = 3,        /* a CUDA runtime call failed (see lbfe_last_cuda_error) */
+    LBFE_ERR_DIVERGED = 4,    /* the device flagged a numerical blow-up */
+    LBFE_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired */
+    LBFE_ERR_STATE = 6        /* call out of order, e.g. step before init */
+} lbfe_status;
+
+typedef enum {
+    LBFE_FP32 = 0,            /* populations stored in FP32 */
+    LBFE_FP16_OFFSET = 1,     /* stored as FP16 offsets f - w_i rho0_s, FP32 compute */
+    LBFE_BF16_OFFSET = 2      /* stored as BF16 offsets f - w_i rho0_s, FP32 compute */
+} lbfe_precision;
+
+typedef enum {
+    LBFE_NEWTONIAN = 0,
+    LBFE_DROPLET_VISCOELASTIC = 1,  /* DV: polymer in component A */
+    LBFE_MATRIX_VISCOELASTIC = 2    /* MV: polymer in component B */
+} lbfe_visco_phase;
+
+/* Parameters of one droplet instance (lattice units). */
+typedef struct {
+    int Lx, Ly, Lz;           /* lattice; the wall gap W is Lz */
+    int visco_phase;          /* lbfe_visco_phase */
+    int precision;            /* lbfe_precision (the same for every instance of a batch) */
+    int reserved0;
+    double R;                 /* droplet radius at rest: reference length of L_p/2R and Ca */
+    double Uw;                /* wall speed; shear rate 2 Uw / W */
+    double G;                 /* Shan-Chen inter-component coupling (> 0 separates) */
+    double eta_M;             /* matrix total dynamic viscosity */
+    double lambda;            /* droplet/matrix total-viscosity ratio (Sec. 2) */
+    double eta_P;             /* polymer viscosity of the viscoelastic phase */
+    double tau_P;             /* polymer relaxation time (> 0) */
+    double L2;                /* FENE-P extensibility L^2 (> 3) */
+    double rho_in;            /* bulk density of a component where it is the majority */
+    double rho_out;           /* bulk density of the dissolved component */
+    double sigma;             /* interfacial tension of G (bookkeeping of Ca, De, tau_em) */
+    double g[3];              /* constant body acceleration (verification hook; 0 normally) */
+    double rho0[2];           /* storage offsets of the reduced-precision forms, per component */
+} lbfe_params;
+
+/* Derived numbers (host arithmetic only). */
+typedef struct {
+    double nu_A, nu_B;        /* solvent kinematic viscosities */
+    double tau_A, tau_B;      /* BGK relaxation times in the two bulk phases */
+    double pi_coef;           /* eta_P / tau_P of the viscoelastic phase */
+    double gamma_dot;         /* 2 Uw / W (Sec. 3) */
+    double Ca;                /* eta_M gamma_dot R / sigma (Sec. 1) */
+    double tau_em;            /* R eta_M / sigma, Eq. 9 */
+    double De;                /* (tau_P / tau_em)(eta_P / eta_M), Eq. 8 */
+} lbfe_derived;
+
+/* Droplet observables of one instance. */
+typedef struct {
+    long long step;           /* steps taken since lbfe_init */
+    double mass[2];           /* sum of rho_A and rho_B over the box (FP64) */
+    double volume;            /* number of droplet cells (rho_A > rho_B) */
+    double centroid[3];       /* droplet centroid; x in [0, Lx) */
+    double M[6];              /* second moments about the centroid: xx, yy, zz, xy, xz, yz */
+    double D;                 /* (a - b)/(a + b), a, b from the extreme eigenvalues of M */
+    double theta_deg;         /* major-axis angle from +x in the x-z plane, (-90, 90] */
+    double Lp;                /* projected length on x (occupied planes, periodic) */
+    double Lp_over_2R;        /* Lp / (2 R) */
+    double t_over_tem;        /* step / tau_em */
+    int necks;                /* interior non-empty minima of the x-profile below half the adjacent maxima */
+    int fragments;            /* separated occupied x-runs holding >= 1% of the volume */
+    int broken;               /* fragments >= 2 */
+    int flags;                /* device status word (bit 0: diverged) */
+} lbfe_obs;
+
+typedef struct lbfe_handle lbfe_handle;
+
+/* Fields for lbfe_get_field / lbfe_set_field (float32 host arrays). */
+enum {
+    LBFE_FIELD_F = 0,         /* populations [2][19][N] (decoded to FP32); get and set */
+    LBFE_FIELD_C = 1,         /* conformation [6][N]; get and set */
+    LBFE_FIELD_RHO = 2,       /* densities [2][N] of the current state; get only */
+    LBFE_FIELD_U = 3          /* velocity (j + F/2)/rho [3][N] of the current state; get only */
+};
+
+const char *lbfe_status_str(lbfe_status s);
+/* Message of the last failing CUDA call in this thread ("" if none). */
+const char *lbfe_last_cuda_error(void);
+/* sizeof() of the structs, so that bindings can check their marshalling. */
+size_t lbfe_params_size(void);
+size_t lbfe_obs_size(void);
+
+/* Validate p and fill the derived numbers.  BAD_PARAM on: a non-positive
+ * lattice size, Lz < 2, a solvent viscosity <= 0 (eta_P too large), BGK
+ * tau <= 1/2, tau_P <= 0, L^2 <= 3, Uw >= 0.1 (Mach limit), an unknown
+ * phase or precision.  out may be NULL. */
+lbfe_status lbfe_derive(const lbfe_params *p, lbfe_derived *out);
+
+/* Device bytes needed by a batch of n instances with parameters p[0..n-1]. */
+lbfe_status lbfe_required_bytes(const lbfe_params *p, int n, size_t *bytes);
+
+/* Create a solver over n instances (n = 1 for a single droplet).  p is
+ * copied; device_block (>= lbfe_required_bytes, 256-byte aligned) is
+ * borrowed until lbfe_destroy; stream is a cudaStream_t or NULL.  All
+ * instances of a batch share p[0].precision. */
+lbfe_status lbfe_create(lbfe_handle **h, const lbfe_params *p, int n, void *device_block,
+                        size_t bytes, void *stream);
+
+/* Initial state of instance k from host densities rho_init[2][N] (float64):
+ * f = f^eq(rho_s, u = 0) and C = I (Sec. 3: droplet at rest when the walls
+ * start).  Resets the step counter.  Copies synchronously from host memory. */
+lbfe_status lbfe_init(lbfe_handle *h, int k, const double *rho_init);
+
+/* Advance every instance by nsteps time steps (asynchronous on the stream). */
+lbfe_status lbfe_step(lbfe_handle *h, long long nsteps);
+
+/* Observables of instance k (synchronises the stream). */
+lbfe_status lbfe_observables(lbfe_handle *h, int k, lbfe_obs *out);
+
+/* DIVERGED if any instance has flagged a blow-up, else OK (synchronises). */
+lbfe_status lbfe_check(lbfe_handle *h);
+
+/* Copy a field of instance k to / from host memory (float32; bytes must be
+ * exactly the field's size).  Synchronises the stream. */
+lbfe_status lbfe_get_field(lbfe_handle *h, int k, int which, void *host_dst, size_t bytes);
+lbfe_status lbfe_set_field(lbfe_handle *h, int k, int which, const void *host_src, size_t bytes);
+
+/* Number of kernel launches one lbfe_step(h, 1) enqueues. */
+int lbfe_launches_per_step(const lbfe_handle *h);
+
+/* Launch shape of the step kernel: column-tile height tile_y in {4, 8, 16}
+ * (tile width 32) and z-chunk depth in planes (0 = automatic: fill the
+ * resident blocks of the GPU about once).  Affects speed only; results are
+ * identical for every shape.  Synchronises the stream. */
+lbfe_status lbfe_tune(lbfe_handle *h, int tile_y, int z_chunk);
+/* Current launch shape (any output may be NULL): tile height, z-chunk of
+ * instance 0, persistent grid size and number of work items. */
+lbfe_status lbfe_launch_config(const lbfe_handle *h, int *tile_y, int *z_chunk, int *grid, int *items);
+
+/* Release the handle (the device block stays the caller's). */
+lbfe_status lbfe_destroy(lbfe_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBFE_H */

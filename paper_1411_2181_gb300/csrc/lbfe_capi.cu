@@ -1,0 +1,625 @@
+// lbfe_capi.cu -- host implementation of the C ABI declared in lbfe.h.
+//
+// The handle owns no device memory: it carves every field out of the block
+// the caller passes to lbfe_create (PyTorch allocates it in the Python
+// binding).  All device work is enqueued on the caller's stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbfe_internal.cuh"
+
+namespace lbfe {
+cudaError_t obs_set_smem_limit(size_t bytes);
+}
+
+using lbfe::InstDev;
+
+namespace {
+
+thread_local std::string g_cuda_err;
+
+lbfe_status cuda_fail(cudaError_t e, const char *where) {
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s: %s", where, cudaGetErrorString(e));
+    g_cuda_err = buf;
+    return LBFE_ERR_CUDA;
+}
+
+#define CK(call)                                                     \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);          \
+    } while (0)
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+size_t elem_bytes(int precision) { return precision == LBFE_FP32 ? 4 : 2; }
+
+struct Derived {
+    double nu_A, nu_B, pi_coef;
+    int visc_comp;
+};
+
+// Sec. 2: lambda = eta_d/eta_M with total viscosities; DV puts eta_P in the
+// droplet (eta_d = eta_A + eta_P, eta_M = eta_B), MV in the matrix
+// (eta_d = eta_A, eta_M = eta_B + eta'_P).  Kinematic viscosities use the
+// bulk total density rho_in + rho_out.
+lbfe_status derive(const lbfe_params &p, Derived &d) {
+    if (p.Lx < 1 || p.Ly < 1 || p.Lz < 2 || p.Lx > 4096) return LBFE_ERR_BAD_PARAM;
+    if ((long long)p.Lx * p.Ly * p.Lz > (1LL << 40)) return LBFE_ERR_BAD_PARAM;
+    if (p.precision < LBFE_FP32 || p.precision > LBFE_BF16_OFFSET) return LBFE_ERR_BAD_PARAM;
+    if (p.visco_phase < 0 || p.visco_phase > 2) return LBFE_ERR_BAD_PARAM;
+    if (!(p.tau_P > 0.0) || !(p.L2 > 3.0) || !(p.rho_in > 0.0) || !(p.rho_out >= 0.0)) return LBFE_ERR_BAD_PARAM;
+    if (!(std::fabs(p.Uw) < 0.1) || !(p.eta_M > 0.0) || !(p.lambda > 0.0) || !(p.eta_P >= 0.0)) return LBFE_ERR_BAD_PARAM;
+    if (!(p.G >= 0.0)) return LBFE_ERR_BAD_PARAM;
+    const double rho_ref = p.rho_in + p.rho_out;
+    const double eta_d = p.lambda * p.eta_M;
+    double eta_A = eta_d, eta_B = p.eta_M;
+    d.pi_coef = 0.0;
+    d.visc_comp = -1;
+    if (p.visco_phase == LBFE_DROPLET_VISCOELASTIC) {
+        eta_A = eta_d - p.eta_P;
+        d.pi_coef = p.eta_P / p.tau_P;
+        d.visc_comp = 0;
+    } else if (p.visco_phase == LBFE_MATRIX_VISCOELASTIC) {
+        eta_B = p.eta_M - p.eta_P;
+        d.pi_coef = p.eta_P / p.tau_P;
+        d.visc_comp = 1;
+    }
+    d.nu_A = eta_A / rho_ref;
+    d.nu_B = eta_B / rho_ref;
+    if (!(d.nu_A > 0.0) || !(d.nu_B > 0.0)) return LBFE_ERR_BAD_PARAM;
+    return LBFE_OK;
+}
+
+struct Layout {
+    size_t inst_off, tile_off, item_off, status_off, mass_off;
+    std::vector<size_t> f_off[2], C_off[2], scratch_off, prof_off, mpart_off;
+    size_t total;
+};
+
+long long stride_of(const lbfe_params &p) {
+    const long long N = (long long)p.Lx * p.Ly * p.Lz;
+    return (N + 63) / 64 * 64;
+}
+
+Layout plan(const lbfe_params *p, int n) {
+    Layout L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, kAlign); return o; };
+    L.inst_off = take(sizeof(InstDev) * (size_t)n);
+    L.tile_off = take(sizeof(int) * (size_t)(n + 1));
+    L.item_off = take(sizeof(int) * (size_t)(n + 1));
+    L.status_off = take(sizeof(unsigned) * 4);
+    L.mass_off = take(sizeof(double) * 2);
+    const size_t eb = elem_bytes(p[0].precision);
+    for (int k = 0; k < n; ++k) {
+        const size_t S = (size_t)stride_of(p[k]);
+        L.f_off[0].push_back(take(eb * 2 * lbfe::Q * S));
+        L.f_off[1].push_back(take(eb * 2 * lbfe::Q * S));
+        L.C_off[0].push_back(take(sizeof(float) * 6 * S));
+        L.C_off[1].push_back(take(sizeof(float) * 6 * S));
+        L.scratch_off.push_back(take(sizeof(float) * 14 * S));
+        L.prof_off.push_back(take(sizeof(unsigned long long) * 6 * (size_t)p[k].Lx));
+        L.mpart_off.push_back(take(sizeof(double) * 2 * lbfe::kObsBlocks));
+    }
+    L.total = off;
+    return L;
+}
+
+// ---- host-side droplet analysis (own implementation; see lbfe.h) -------
+
+void sym_eig3(const double M[6], double ev[3], double V[3][3]) {
+    double A[3][3] = {{M[0], M[3], M[4]}, {M[3], M[1], M[5]}, {M[4], M[5], M[2]}};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) V[i][j] = i == j ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 64; ++sweep) {
+        const double off = std::fabs(A[0][1]) + std::fabs(A[0][2]) + std::fabs(A[1][2]);
+        if (off == 0.0) break;
+        for (int pp = 0; pp < 2; ++pp)
+            for (int qq = pp + 1; qq < 3; ++qq) {
+                if (A[pp][qq] == 0.0) continue;
+                const double theta = 0.5 * std::atan2(2.0 * A[pp][qq], A[qq][qq] - A[pp][pp]);
+                const double c = std::cos(theta), s = std::sin(theta);
+                // rotation in the (pp, qq) plane that zeroes A[pp][qq]
+                for (int k = 0; k < 3; ++k) {
+                    const double akp = A[k][pp], akq = A[k][qq];
+                    A[k][pp] = c * akp - s * akq;
+                    A[k][qq] = s * akp + c * akq;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    const double apk = A[pp][k], aqk = A[qq][k];
+                    A[pp][k] = c * apk - s * aqk;
+                    A[qq][k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    const double vkp = V[k][pp], vkq = V[k][qq];
+                    V[k][pp] = c * vkp - s * vkq;
+                    V[k][qq] = s * vkp + c * vkq;
+                }
+            }
+    }
+    for (int i = 0; i < 3; ++i) ev[i] = A[i][i];
+}
+
+int wrapi(int a, int L) { return ((a % L) + L) % L; }
+
+// From the per-plane droplet counts A(x): projected length, start of the
+// unwrapped axis (first occupied plane after the longest empty run), neck
+// count and fragments holding >= 1% of the volume.
+void analyse_profile(const std::vector<long long> &A, int &Lp, int &start, int &necks, int &frags) {
+    const int Lx = (int)A.size();
+    long long V = 0;
+    for (long long a : A) V += a;
+    Lp = start = necks = frags = 0;
+    if (V == 0) return;
+    int gap = 0, gap_end = 0;
+    for (int x = 0; x < Lx; ++x) {
+        if (A[x] != 0 || A[wrapi(x - 1, Lx)] == 0) continue;  // empty run starts at x
+        int len = 0;
+        while (len < Lx && A[wrapi(x + len, Lx)] == 0) ++len;
+        if (len > gap) { gap = len; gap_end = x + len; }
+    }
+    start = gap > 0 ? wrapi(gap_end, Lx) : 0;
+    Lp = Lx - gap;
+    std::vector<long long> seq(Lp);
+    for (int q = 0; q < Lp; ++q) seq[q] = A[wrapi(start + q, Lx)];
+    for (int q = 0; q < Lp;) {
+        if (seq[q] == 0) { ++q; continue; }
+        long long vol = 0;
+        while (q < Lp && seq[q] != 0) vol += seq[q++];
+        if (100 * vol >= V) ++frags;
+    }
+    // plateau-compressed profile framed by empty planes
+    std::vector<long long> c{0};
+    for (long long v : seq)
+        if (v != c.back()) c.push_back(v);
+    if (c.back() != 0) c.push_back(0);
+    long long prev_max = -1, dip = 0;
+    bool have_dip = false;
+    for (size_t q = 1; q + 1 < c.size(); ++q) {
+        if (c[q] > c[q - 1] && c[q] > c[q + 1]) {
+            if (have_dip && prev_max >= 0 && dip > 0 && 2 * dip < std::min(prev_max, c[q])) ++necks;
+            prev_max = c[q];
+            have_dip = false;
+        } else if (c[q] < c[q - 1] && c[q] < c[q + 1]) {
+            dip = c[q];
+            have_dip = true;
+        }
+    }
+}
+
+}  // namespace
+
+struct lbfe_handle {
+    int n = 0, precision = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<lbfe_params> params;
+    std::vector<InstDev> inst;
+    std::vector<long long> steps;
+    std::vector<char> ready;
+    char *base = nullptr;
+    Layout layout;
+    InstDev *inst_dev = nullptr;
+    int *tile_off = nullptr;
+    int total_tiles = 0;
+    int *item_off = nullptr;
+    int total_items = 0, fused_grid = 0, tile_y = 8, z_chunk_req = 0, num_sms = 0, blocks_per_sm = 0;
+    unsigned *status = nullptr;
+    double *mass = nullptr;
+    int cur = 0;
+
+    lbfe::LaunchCtx ctx() const {
+        lbfe::LaunchCtx c;
+        c.inst_dev = inst_dev;
+        c.inst_host = inst.data();
+        c.tile_off = tile_off;
+        c.n = n;
+        c.total_tiles = total_tiles;
+        c.precision = precision;
+        c.status = status;
+        c.stream = stream;
+        c.item_off = item_off;
+        c.total_items = total_items;
+        c.fused_grid = fused_grid;
+        c.tile_y = tile_y;
+        return c;
+    }
+};
+
+// Work items of the fused kernel: per instance ceil(Lx/32) x ceil(Ly/TY)
+// column tiles times nzc z-chunks.  Without a requested chunk depth, nzc is
+// chosen so that the items fill the resident blocks of the GPU about once
+// (chunks of at least 8 planes).
+static lbfe_status configure_fused(lbfe_handle *h, int tile_y, int z_chunk) {
+    if (tile_y != 4 && tile_y != 8 && tile_y != 16) return LBFE_ERR_BAD_PARAM;
+    if (z_chunk < 0) return LBFE_ERR_BAD_PARAM;
+    int bps = 0;
+    cudaError_t e = lbfe::fused_prepare(tile_y, h->precision, &bps);
+    if (e != cudaSuccess) return cuda_fail(e, "fused_prepare");
+    if (bps < 1) return LBFE_ERR_BAD_PARAM;
+    long long columns = 0;
+    for (auto &I : h->inst) {
+        I.ntx = (I.Lx + 31) / 32;
+        I.nty = (I.Ly + tile_y - 1) / tile_y;
+        columns += (long long)I.ntx * I.nty;
+    }
+    const long long slots = (long long)h->num_sms * bps;
+    std::vector<int> off(h->n + 1, 0);
+    for (int k = 0; k < h->n; ++k) {
+        InstDev &I = h->inst[k];
+        int zc = z_chunk;
+        if (zc == 0) {
+            long long nz = (slots + columns / 2) / columns;
+            if (nz < 1) nz = 1;
+            zc = (int)((I.Lz + nz - 1) / nz);
+            if (zc < 8) zc = 8;
+        }
+        if (zc > I.Lz) zc = I.Lz;
+        I.zc = zc;
+        I.nzc = (I.Lz + zc - 1) / zc;
+        const long long items = (long long)I.ntx * I.nty * I.nzc;
+        if (off[k] + items > (long long)0x7fffffff) return LBFE_ERR_BAD_PARAM;
+        off[k + 1] = off[k] + (int)items;
+    }
+    h->tile_y = tile_y;
+    h->z_chunk_req = z_chunk;
+    h->blocks_per_sm = bps;
+    h->total_items = off[h->n];
+    h->fused_grid = (int)std::min<long long>(h->total_items, slots);
+    e = cudaMemcpyAsync(h->inst_dev, h->inst.data(), sizeof(InstDev) * h->n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->item_off, off.data(), sizeof(int) * (h->n + 1), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "configure_fused");
+    return LBFE_OK;
+}
+
+extern "C" {
+
+const char *lbfe_status_str(lbfe_status s) {
+    switch (s) {
+        case LBFE_OK: return "ok";
+        case LBFE_ERR_BAD_PARAM: return "invalid argument or parameters";
+        case LBFE_ERR_NO_MEMORY: return "device block smaller than required";
+        case LBFE_ERR_CUDA: return "CUDA runtime error";
+        case LBFE_ERR_DIVERGED: return "simulation diverged";
+        case LBFE_ERR_TIMEOUT: return "device wait timed out";
+        case LBFE_ERR_STATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+const char *lbfe_last_cuda_error(void) { return g_cuda_err.c_str(); }
+size_t lbfe_params_size(void) { return sizeof(lbfe_params); }
+size_t lbfe_obs_size(void) { return sizeof(lbfe_obs); }
+
+lbfe_status lbfe_derive(const lbfe_params *p, lbfe_derived *out) {
+    if (!p) return LBFE_ERR_BAD_PARAM;
+    Derived d;
+    lbfe_status s = derive(*p, d);
+    if (s != LBFE_OK) return s;
+    const double tauA = 3.0 * d.nu_A + 0.5, tauB = 3.0 * d.nu_B + 0.5;
+    if (!(tauA > 0.5) || !(tauB > 0.5)) return LBFE_ERR_BAD_PARAM;
+    if (out) {
+        out->nu_A = d.nu_A;
+        out->nu_B = d.nu_B;
+        out->tau_A = tauA;
+        out->tau_B = tauB;
+        out->pi_coef = d.pi_coef;
+        out->gamma_dot = 2.0 * p->Uw / p->Lz;
+        out->Ca = p->sigma > 0 ? p->eta_M * out->gamma_dot * p->R / p->sigma : 0.0;
+        out->tau_em = p->sigma > 0 ? p->R * p->eta_M / p->sigma : 0.0;
+        out->De = out->tau_em > 0 ? (p->tau_P / out->tau_em) * (p->eta_P / p->eta_M) : 0.0;
+    }
+    return LBFE_OK;
+}
+
+lbfe_status lbfe_required_bytes(const lbfe_params *p, int n, size_t *bytes) {
+    if (!p || n < 1 || !bytes) return LBFE_ERR_BAD_PARAM;
+    for (int k = 0; k < n; ++k) {
+        lbfe_status s = lbfe_derive(p + k, nullptr);
+        if (s != LBFE_OK) return s;
+        if (p[k].precision != p[0].precision) return LBFE_ERR_BAD_PARAM;
+    }
+    *bytes = plan(p, n).total;
+    return LBFE_OK;
+}
+
+lbfe_status lbfe_create(lbfe_handle **hp, const lbfe_params *p, int n, void *device_block, size_t bytes,
+                        void *stream) {
+    if (!hp) return LBFE_ERR_BAD_PARAM;
+    *hp = nullptr;
+    size_t need = 0;
+    lbfe_status s = lbfe_required_bytes(p, n, &need);
+    if (s != LBFE_OK) return s;
+    if (!device_block || ((uintptr_t)device_block % kAlign) != 0) return LBFE_ERR_BAD_PARAM;
+    if (bytes < need) return LBFE_ERR_NO_MEMORY;
+    lbfe_handle *h = new (std::nothrow) lbfe_handle;
+    if (!h) return LBFE_ERR_NO_MEMORY;
+    h->n = n;
+    h->precision = p[0].precision;
+    h->stream = (cudaStream_t)stream;
+    h->params.assign(p, p + n);
+    h->steps.assign(n, 0);
+    h->ready.assign(n, 0);
+    h->base = (char *)device_block;
+    h->layout = plan(p, n);
+    const Layout &L = h->layout;
+    h->inst_dev = (InstDev *)(h->base + L.inst_off);
+    h->tile_off = (int *)(h->base + L.tile_off);
+    h->item_off = (int *)(h->base + L.item_off);
+    h->status = (unsigned *)(h->base + L.status_off);
+    h->mass = (double *)(h->base + L.mass_off);
+    std::vector<int> toff(n + 1, 0);
+    int maxLx = 0;
+    for (int k = 0; k < n; ++k) {
+        Derived d;
+        derive(p[k], d);
+        InstDev I;
+        memset(&I, 0, sizeof I);
+        I.Lx = p[k].Lx; I.Ly = p[k].Ly; I.Lz = p[k].Lz;
+        I.visc_comp = d.visc_comp;
+        I.N = (long long)p[k].Lx * p[k].Ly * p[k].Lz;
+        I.S = stride_of(p[k]);
+        I.f[0] = h->base + L.f_off[0][k];
+        I.f[1] = h->base + L.f_off[1][k];
+        I.C[0] = (float *)(h->base + L.C_off[0][k]);
+        I.C[1] = (float *)(h->base + L.C_off[1][k]);
+        float *scr = (float *)(h->base + L.scratch_off[k]);
+        I.rho = scr;
+        I.jm = scr + 2 * I.S;
+        I.u = scr + 5 * I.S;
+        I.F = scr + 8 * I.S;
+        I.prof = (unsigned long long *)(h->base + L.prof_off[k]);
+        I.mpart = (double *)(h->base + L.mpart_off[k]);
+        I.G = (float)p[k].G;
+        I.Uw = (float)p[k].Uw;
+        I.nu_A = (float)d.nu_A;
+        I.nu_B = (float)d.nu_B;
+        I.pi_coef = (float)d.pi_coef;
+        I.L2 = (float)p[k].L2;
+        I.inv_tauP = (float)(1.0 / p[k].tau_P);
+        I.gx = (float)p[k].g[0]; I.gy = (float)p[k].g[1]; I.gz = (float)p[k].g[2];
+        I.rho0[0] = (float)p[k].rho0[0];
+        I.rho0[1] = (float)p[k].rho0[1];
+        h->inst.push_back(I);
+        toff[k + 1] = toff[k] + (int)((I.N + lbfe::kBlock - 1) / lbfe::kBlock);
+        if (p[k].Lx > maxLx) maxLx = p[k].Lx;
+    }
+    h->total_tiles = toff[n];
+    cudaError_t e = cudaMemcpyAsync(h->inst_dev, h->inst.data(), sizeof(InstDev) * n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->tile_off, toff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(unsigned) * 4, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    const size_t smem = sizeof(unsigned long long) * 6 * (size_t)maxLx;
+    if (e == cudaSuccess && smem > 48 * 1024) e = lbfe::obs_set_smem_limit(smem);
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "lbfe_create");
+    }
+    lbfe_status st = configure_fused(h, 8, 0);
+    if (st != LBFE_OK) {
+        delete h;
+        return st;
+    }
+    *hp = h;
+    return LBFE_OK;
+}
+
+lbfe_status lbfe_init(lbfe_handle *h, int k, const double *rho_init) {
+    if (!h || k < 0 || k >= h->n || !rho_init) return LBFE_ERR_BAD_PARAM;
+    const InstDev &I = h->inst[k];
+    // stage the densities (FP64) in the instance's scratch, then build f^eq
+    double *stage = (double *)I.rho;
+    CK(cudaMemcpyAsync(stage, rho_init, sizeof(double) * 2 * (size_t)I.N, cudaMemcpyHostToDevice, h->stream));
+    CK(lbfe::launch_init(h->ctx(), k, stage, h->cur));
+    CK(cudaStreamSynchronize(h->stream));
+    h->steps[k] = 0;
+    h->ready[k] = 1;
+    return LBFE_OK;
+}
+
+lbfe_status lbfe_step(lbfe_handle *h, long long nsteps) {
+    if (!h || nsteps < 0) return LBFE_ERR_BAD_PARAM;
+    for (int k = 0; k < h->n; ++k)
+        if (!h->ready[k]) return LBFE_ERR_STATE;
+    const lbfe::LaunchCtx c = h->ctx();
+    for (long long t = 0; t < nsteps; ++t) {
+        CK(lbfe::launch_fused(c, h->cur));
+        h->cur ^= 1;
+    }
+    for (int k = 0; k < h->n; ++k) h->steps[k] += nsteps;
+    return LBFE_OK;
+}
+
+lbfe_status lbfe_check(lbfe_handle *h) {
+    if (!h) return LBFE_ERR_BAD_PARAM;
+    unsigned st = 0;
+    CK(cudaMemcpyAsync(&st, h->status, sizeof st, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return (st & lbfe::kFlagDiverged) ? LBFE_ERR_DIVERGED : LBFE_OK;
+}
+
+lbfe_status lbfe_observables(lbfe_handle *h, int k, lbfe_obs *out) {
+    if (!h || k < 0 || k >= h->n || !out) return LBFE_ERR_BAD_PARAM;
+    if (!h->ready[k]) return LBFE_ERR_STATE;
+    const InstDev &I = h->inst[k];
+    const lbfe_params &p = h->params[k];
+    CK(lbfe::launch_observables(h->ctx(), k, h->cur, h->mass));
+    std::vector<unsigned long long> prof(6 * (size_t)I.Lx);
+    double mass[2];
+    unsigned st = 0;
+    CK(cudaMemcpyAsync(prof.data(), I.prof, sizeof(unsigned long long) * prof.size(), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(mass, h->mass, sizeof mass, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&st, h->status, sizeof st, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+
+    memset(out, 0, sizeof *out);
+    out->step = h->steps[k];
+    out->mass[0] = mass[0];
+    out->mass[1] = mass[1];
+    out->flags = (int)st;
+    const int Lx = I.Lx;
+    std::vector<long long> A(Lx);
+    for (int x = 0; x < Lx; ++x) A[x] = (long long)prof[x];
+    int Lp, start, necks, frags;
+    analyse_profile(A, Lp, start, necks, frags);
+    out->Lp = Lp;
+    out->Lp_over_2R = p.R > 0 ? Lp / (2.0 * p.R) : 0.0;
+    out->necks = necks;
+    out->fragments = frags;
+    out->broken = frags >= 2;
+    Derived d;
+    derive(p, d);
+    const double tem = p.sigma > 0 ? p.R * p.eta_M / p.sigma : 0.0;
+    out->t_over_tem = tem > 0 ? (double)h->steps[k] / tem : 0.0;
+    // moments with the unwrapped x' = (x - start) mod Lx
+    double V = 0, sx = 0, sy = 0, sz = 0, sxx = 0, syy = 0, szz = 0, sxy = 0, sxz = 0, syz = 0;
+    for (int x = 0; x < Lx; ++x) {
+        const double xp = (double)wrapi(x - start, Lx);
+        const double a = (double)prof[x];
+        V += a;
+        sx += xp * a;
+        sxx += xp * xp * a;
+        sy += (double)prof[Lx + x];
+        sz += (double)prof[2 * Lx + x];
+        syy += (double)prof[3 * Lx + x];
+        szz += (double)prof[4 * Lx + x];
+        syz += (double)prof[5 * Lx + x];
+        sxy += xp * (double)prof[Lx + x];
+        sxz += xp * (double)prof[2 * Lx + x];
+    }
+    out->volume = V;
+    if (V > 0) {
+        const double cx = sx / V, cy = sy / V, cz = sz / V;
+        out->centroid[0] = std::fmod(cx + start, (double)Lx);
+        out->centroid[1] = cy;
+        out->centroid[2] = cz;
+        double *M = out->M;
+        M[0] = sxx - V * cx * cx; M[1] = syy - V * cy * cy; M[2] = szz - V * cz * cz;
+        M[3] = sxy - V * cx * cy; M[4] = sxz - V * cx * cz; M[5] = syz - V * cy * cz;
+        double ev[3], Vec[3][3];
+        sym_eig3(M, ev, Vec);
+        int imax = 0, imin = 0;
+        for (int q = 1; q < 3; ++q) {
+            if (ev[q] > ev[imax]) imax = q;
+            if (ev[q] < ev[imin]) imin = q;
+        }
+        const double a = std::sqrt(5.0 * std::fmax(ev[imax], 0.0) / V);
+        const double b = std::sqrt(5.0 * std::fmax(ev[imin], 0.0) / V);
+        out->D = (a + b) > 0 ? (a - b) / (a + b) : 0.0;
+        double th = std::atan2(Vec[2][imax], Vec[0][imax]) * 180.0 / M_PI;
+        if (th <= -90.0) th += 180.0;
+        if (th > 90.0) th -= 180.0;
+        out->theta_deg = th;
+    }
+    return (st & lbfe::kFlagDiverged) ? LBFE_ERR_DIVERGED : LBFE_OK;
+}
+
+lbfe_status lbfe_get_field(lbfe_handle *h, int k, int which, void *host_dst, size_t bytes) {
+    if (!h || k < 0 || k >= h->n || !host_dst) return LBFE_ERR_BAD_PARAM;
+    if (!h->ready[k]) return LBFE_ERR_STATE;
+    const InstDev &I = h->inst[k];
+    const size_t N = (size_t)I.N, S = (size_t)I.S;
+    float *dst = (float *)host_dst;
+    const lbfe::LaunchCtx c = h->ctx();
+    switch (which) {
+        case LBFE_FIELD_F: {
+            if (bytes != sizeof(float) * 2 * lbfe::Q * N) return LBFE_ERR_BAD_PARAM;
+            float *tmp = I.u;  // scratch slice of >= N floats
+            for (int s = 0; s < 2; ++s)
+                for (int i = 0; i < lbfe::Q; ++i) {
+                    CK(lbfe::launch_decode_pop(c, k, h->cur, s, i, tmp));
+                    CK(cudaMemcpyAsync(dst + (size_t)(s * lbfe::Q + i) * N, tmp, sizeof(float) * N,
+                                       cudaMemcpyDeviceToHost, h->stream));
+                    CK(cudaStreamSynchronize(h->stream));
+                }
+            return LBFE_OK;
+        }
+        case LBFE_FIELD_C:
+            if (bytes != sizeof(float) * 6 * N) return LBFE_ERR_BAD_PARAM;
+            CK(cudaMemcpy2DAsync(dst, sizeof(float) * N, I.C[h->cur], sizeof(float) * S, sizeof(float) * N, 6,
+                                 cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            return LBFE_OK;
+        case LBFE_FIELD_RHO:
+        case LBFE_FIELD_U: {
+            const int rows = which == LBFE_FIELD_RHO ? 2 : 3;
+            if (bytes != sizeof(float) * rows * N) return LBFE_ERR_BAD_PARAM;
+            CK(lbfe::launch_moments(c, h->cur));
+            if (which == LBFE_FIELD_U) CK(lbfe::launch_forces(c, h->cur));
+            const float *src = which == LBFE_FIELD_RHO ? I.rho : I.u;
+            CK(cudaMemcpy2DAsync(dst, sizeof(float) * N, src, sizeof(float) * S, sizeof(float) * N, rows,
+                                 cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            return LBFE_OK;
+        }
+        default:
+            return LBFE_ERR_BAD_PARAM;
+    }
+}
+
+lbfe_status lbfe_set_field(lbfe_handle *h, int k, int which, const void *host_src, size_t bytes) {
+    if (!h || k < 0 || k >= h->n || !host_src) return LBFE_ERR_BAD_PARAM;
+    if (!h->ready[k]) return LBFE_ERR_STATE;
+    const InstDev &I = h->inst[k];
+    const size_t N = (size_t)I.N, S = (size_t)I.S;
+    const float *src = (const float *)host_src;
+    switch (which) {
+        case LBFE_FIELD_F: {
+            if (bytes != sizeof(float) * 2 * lbfe::Q * N) return LBFE_ERR_BAD_PARAM;
+            float *tmp = I.u;
+            const lbfe::LaunchCtx c = h->ctx();
+            for (int s = 0; s < 2; ++s)
+                for (int i = 0; i < lbfe::Q; ++i) {
+                    CK(cudaMemcpyAsync(tmp, src + (size_t)(s * lbfe::Q + i) * N, sizeof(float) * N,
+                                       cudaMemcpyHostToDevice, h->stream));
+                    CK(lbfe::launch_encode_pop(c, k, h->cur, s, i, tmp));
+                    CK(cudaStreamSynchronize(h->stream));
+                }
+            return LBFE_OK;
+        }
+        case LBFE_FIELD_C:
+            if (bytes != sizeof(float) * 6 * N) return LBFE_ERR_BAD_PARAM;
+            CK(cudaMemcpy2DAsync(I.C[h->cur], sizeof(float) * S, src, sizeof(float) * N, sizeof(float) * N, 6,
+                                 cudaMemcpyHostToDevice, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            return LBFE_OK;
+        default:
+            return LBFE_ERR_BAD_PARAM;
+    }
+}
+
+int lbfe_launches_per_step(const lbfe_handle *h) { return h ? 1 : 0; }
+
+lbfe_status lbfe_tune(lbfe_handle *h, int tile_y, int z_chunk) {
+    if (!h) return LBFE_ERR_BAD_PARAM;
+    return configure_fused(h, tile_y, z_chunk);
+}
+
+lbfe_status lbfe_launch_config(const lbfe_handle *h, int *tile_y, int *z_chunk, int *grid, int *items) {
+    if (!h) return LBFE_ERR_BAD_PARAM;
+    if (tile_y) *tile_y = h->tile_y;
+    if (z_chunk) *z_chunk = h->inst[0].zc;
+    if (grid) *grid = h->fused_grid;
+    if (items) *items = h->total_items;
+    return LBFE_OK;
+}
+
+lbfe_status lbfe_destroy(lbfe_handle *h) {
+    if (!h) return LBFE_ERR_BAD_PARAM;
+    cudaStreamSynchronize(h->stream);
+    delete h;
+    return LBFE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,130 @@
+// lbfe_internal.cuh -- device-side definitions shared by the CUDA
+// translation units of liblbfe: the D3Q19 lattice, the storage forms of the
+// populations, the per-instance descriptor and the step launchers.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lbfe.h"
+
+namespace lbfe {
+
+constexpr int Q = 19;
+
+// D3Q19 velocity set in the interface order of lbfe.h (rest, 6 faces,
+// 12 edges; the opposite of i > 0 is i + 1 for odd i, i - 1 for even i).
+__host__ __device__ constexpr int cx(int i) {
+    constexpr int t[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+    return t[i];
+}
+__host__ __device__ constexpr int cy(int i) {
+    constexpr int t[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+    return t[i];
+}
+__host__ __device__ constexpr int cz(int i) {
+    constexpr int t[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+    return t[i];
+}
+// weights 1/3 (rest), 1/18 (faces), 1/36 (edges); c_s^2 = 1/3
+__host__ __device__ constexpr float wq(int i) {
+    return i == 0 ? 1.0f / 3.0f : (i <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
+}
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
+// Storage forms of the populations.  FP32 stores f itself; the reduced
+// forms store f - w_i rho0_s rounded to nearest even and decode in FP32.
+template <typename T> struct Store;
+template <> struct Store<float> {
+    static constexpr bool offset = false;
+    static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ float ld_plain(const float *p) { return *p; }
+    static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+};
+template <> struct Store<__half> {
+    static constexpr bool offset = true;
+    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float ld_plain(const __half *p) { return __half2float(*p); }
+    static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
+};
+template <> struct Store<__nv_bfloat16> {
+    static constexpr bool offset = true;
+    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ float ld_plain(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+// Device descriptor of one instance (all pointers into the caller's block).
+struct InstDev {
+    int Lx, Ly, Lz, visc_comp;       // visc_comp: 0 (A), 1 (B), -1 Newtonian
+    long long N, S;                  // cells, padded stride of one field (multiple of 64)
+    void *f[2];                      // populations [2][19][S] in the storage type, ping-pong
+    float *C[2];                     // conformation [6][S], ping-pong
+    float *rho;                      // scratch [2][S]
+    float *jm;                       // scratch [3][S] total momentum
+    float *u;                        // scratch [3][S]
+    float *F;                        // scratch [2][3][S] per-component total force
+    unsigned long long *prof;        // observables: [6][Lx] per-plane integer sums
+    double *mpart;                   // observables: [2][kObsBlocks] mass partials
+    float G, Uw, nu_A, nu_B;         // Shan-Chen coupling, wall speed, solvent viscosities
+    float pi_coef, L2, inv_tauP;     // eta_P/tau_P, L^2, 1/tau_P
+    float gx, gy, gz;                // body acceleration
+    float rho0[2];                   // storage offsets
+    int ntx, nty, nzc, zc;           // fused kernel: column tiles in x, y; z-chunks and their depth
+};
+
+constexpr int kBlock = 256;          // threads per block of the cell-per-thread kernels
+constexpr int kObsBlocks = 304;      // 2 x 152 SMs for the observables reduction
+
+__device__ __forceinline__ int wrapi(int a, int L) { return a < 0 ? a + L : (a >= L ? a - L : a); }
+
+// Instance owning block b of a tiled launch (tile_off[k] = first block of k).
+__device__ __forceinline__ int find_inst(const int *tile_off, int n, int b) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(tile_off + mid) <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Peterlin factor f = (L^2 - 3)/(L^2 - tr C) of Eq. 2, evaluated in FP64
+// when L^2 - tr C falls below 1e-2 L^2 (close to the extensibility limit).
+__device__ __forceinline__ float peterlin(float L2, float cxx, float cyy, float czz) {
+    float tr = cxx + cyy + czz;
+    float den = L2 - tr;
+    if (den < 1e-2f * L2) {
+        double dd = (double)L2 - ((double)cxx + (double)cyy + (double)czz);
+        return (float)(((double)L2 - 3.0) / dd);
+    }
+    return (L2 - 3.0f) / den;
+}
+
+// Status bits written by the kernels into the handle's status word.
+constexpr unsigned kFlagDiverged = 1u;
+
+// Launchers (lbfe_fused.cu, lbfe_fields.cu, lbfe_obs.cu).
+struct LaunchCtx {
+    const InstDev *inst_dev;         // device copy of the descriptors
+    const InstDev *inst_host;        // host copy
+    const int *tile_off;             // device [n+1]
+    int n, total_tiles, precision;
+    unsigned *status;                // device status word
+    cudaStream_t stream;
+    const int *item_off;             // device [n+1]: first fused work item of each instance
+    int total_items, fused_grid, tile_y;
+};
+cudaError_t launch_fused(const LaunchCtx &c, int cur);
+// Shared memory and resident blocks per SM of the fused kernel for a tile height.
+size_t fused_smem_bytes(int tile_y);
+cudaError_t fused_prepare(int tile_y, int precision, int *blocks_per_sm);
+cudaError_t launch_moments(const LaunchCtx &c, int cur);
+cudaError_t launch_forces(const LaunchCtx &c, int cur);
+cudaError_t launch_init(const LaunchCtx &c, int k, const double *rho_dev, int cur);
+cudaError_t launch_decode_pop(const LaunchCtx &c, int k, int cur, int s, int i, float *dst);
+cudaError_t launch_encode_pop(const LaunchCtx &c, int k, int cur, int s, int i, const float *src);
+cudaError_t launch_observables(const LaunchCtx &c, int k, int cur, double *mass_out_dev);
+
+}  // namespace lbfe

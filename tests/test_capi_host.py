@@ -1,0 +1,80 @@
+"""The C ABI library loads and exports every symbol ``include/lbfe.h``
+declares; host-side validation works without a GPU (no compute calls)."""
+import ctypes as ct
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lbfe():
+    from paper_1411_2181_gb300 import build
+    build.build()
+    from paper_1411_2181_gb300 import lbfe as L
+    return L
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "lbfe.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbfe_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported(lbfe):
+    names = declared_functions()
+    assert len(names) >= 14
+    lib = ct.CDLL(lbfe.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_struct_sizes_match(lbfe):
+    assert lbfe._lib.lbfe_params_size() == ct.sizeof(lbfe.CParams)
+    assert lbfe._lib.lbfe_obs_size() == ct.sizeof(lbfe.CObs)
+
+
+def test_parameter_validation_on_host(lbfe):
+    from paper_1411_2181_gb300 import configs
+    p, _, _ = configs.config1()
+    d = lbfe.derive(p)
+    # Sec. 1 / Eq. 9 / Eq. 8 bookkeeping
+    assert abs(d["gamma_dot"] - 2 * p.Uw / p.Lz) < 1e-15
+    assert abs(d["Ca"] - 0.1) < 1e-12
+    assert abs(d["tau_em"] - p.R * p.eta_M / p.sigma) < 1e-9
+    assert abs(d["De"] - 1.0) < 1e-12
+    assert d["tau_A"] > 0.5 and d["tau_B"] > 0.5
+    bad = [dict(Lz=1), dict(tau_P=0.0), dict(L2=3.0), dict(Uw=0.2), dict(eta_P=10.0),
+           dict(visco_phase=5), dict(precision=9), dict(eta_M=-1.0), dict(Lx=0)]
+    from dataclasses import replace
+    for kw in bad:
+        with pytest.raises(lbfe.LbfeError) as ei:
+            lbfe.derive(replace(p, **kw))
+        assert ei.value.status == lbfe.ERR_BAD_PARAM, kw
+
+
+def test_required_bytes_and_batch_precision_rule(lbfe):
+    from dataclasses import replace
+    from paper_1411_2181_gb300 import configs
+    p, _, _ = configs.config1()
+    n1 = lbfe.required_bytes([p])
+    n2 = lbfe.required_bytes([p, p])
+    assert n2 > n1 > p.N * (2 * 19 * 4 * 2 + 6 * 4 * 2)
+    with pytest.raises(lbfe.LbfeError):
+        lbfe.required_bytes([p, replace(p, precision=1)])
+    half = lbfe.required_bytes([replace(p, precision=1)])
+    assert half < n1
+
+
+def test_create_rejects_small_or_misaligned_block(lbfe):
+    from paper_1411_2181_gb300 import configs
+    p, _, _ = configs.config1()
+    arr = (lbfe.CParams * 1)(lbfe._to_c(p))
+    h = ct.c_void_p()
+    need = lbfe.required_bytes([p])
+    # never dereferenced: both are rejected before any CUDA call
+    assert lbfe._lib.lbfe_create(ct.byref(h), arr, 1, ct.c_void_p(4096), need - 1, None) == lbfe.ERR_NO_MEMORY
+    assert lbfe._lib.lbfe_create(ct.byref(h), arr, 1, ct.c_void_p(4096 + 8), need, None) == lbfe.ERR_BAD_PARAM
+    assert lbfe._lib.lbfe_create(ct.byref(h), arr, 0, ct.c_void_p(4096), need, None) == lbfe.ERR_BAD_PARAM

@@ -1,0 +1,205 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle."""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1411_2181_gb300 import configs, synth
+from tests.helpers import component_report, norm_err, random_populations, tensor_err
+
+pytestmark = pytest.mark.gpu
+
+TOL_500 = 1e-5       # FP32 after 500 steps, normalised per population / component
+TOL_FEW = 2e-6       # FP32 after a few steps
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1411_2181_gb300 import build
+    build.build()
+    from paper_1411_2181_gb300 import lbfe
+    return lbfe
+
+
+def run_pair(L, p, rho=None, steps=1, f0=None, C0=None):
+    """Advance the GPU and the oracle from the same state; return both."""
+    s = L.Solver(p)
+    orc = O.Oracle(p.oracle_dict())
+    if rho is None:
+        rho = np.ones((2, p.Lz, p.Ly, p.Lx))
+    s.init(0, rho)
+    orc.init(rho)
+    if f0 is not None:
+        s.set_field(0, L.FIELD_F, f0)
+        orc.f[:] = f0
+    if C0 is not None:
+        s.set_field(0, L.FIELD_C, C0)
+        orc.C[:] = C0
+    # the GPU starts from the FP32-rounded initial state
+    orc.f[:] = s.get_field(0, L.FIELD_F)
+    orc.C[:] = s.get_field(0, L.FIELD_C)
+    s.step(steps)
+    orc.step(steps)
+    return s, orc
+
+
+def test_config1_parity_500_steps(L):
+    """32^3, DV, De = 1, 500 steps: populations and conformation within 1e-5
+    (normalised) of the FP64 oracle."""
+    p, rho, steps = configs.config1()
+    s, orc = run_pair(L, p, rho, steps)
+    C = s.get_field(0, L.FIELD_C)
+    ef = norm_err(s.get_field(0, L.FIELD_F), orc.f, 2)
+    eC = tensor_err(C, orc.C)
+    print(f"config1 500 steps: f {ef:.3e}, C {eC:.3e};", component_report(C, orc.C))
+    assert ef < TOL_500 and eC < TOL_500, (ef, eC, component_report(C, orc.C))
+    assert s.check() == L.OK
+
+
+@pytest.mark.parametrize("shape", [(7, 5, 6), (13, 9, 4), (33, 17, 11), (64, 3, 2)])
+@pytest.mark.parametrize("phase", [0, 1, 2])
+def test_random_state_few_steps_ragged(L, shape, phase):
+    """Arbitrary non-equilibrium populations and conformation on boxes whose
+    sizes do not divide the thread blocks; moving walls; every phase."""
+    Lx, Ly, Lz = shape
+    p = L.Params(Lx=Lx, Ly=Ly, Lz=Lz, R=2.0, Uw=0.03, G=3.1, eta_M=0.4, lambda_=1.3, eta_P=0.15,
+                 tau_P=6.0, L2=40.0, visco_phase=phase, g=(1e-4, -3e-5, 2e-5))
+    f0, C0 = random_populations(shape, seed=sum(shape) + phase)
+    s, orc = run_pair(L, p, None, 1, f0, C0)
+    assert norm_err(s.get_field(0, L.FIELD_F), orc.f, 2) < TOL_FEW
+    assert tensor_err(s.get_field(0, L.FIELD_C), orc.C) < TOL_FEW
+    s.step(4)
+    orc.step(4)
+    assert norm_err(s.get_field(0, L.FIELD_F), orc.f, 2) < 5 * TOL_FEW
+    assert tensor_err(s.get_field(0, L.FIELD_C), orc.C) < 5 * TOL_FEW
+
+
+def test_velocity_and_density_fields(L):
+    """The velocity (j + F/2)/rho and densities the GPU reports for a state
+    match the oracle's intermediate fields."""
+    shape = (12, 10, 8)
+    p = L.Params(Lx=12, Ly=10, Lz=8, R=2.0, Uw=0.02, G=3.1, eta_M=0.5, eta_P=0.2, tau_P=5.0,
+                 L2=50.0, visco_phase=2)
+    f0, C0 = random_populations(shape, seed=9)
+    s, orc = run_pair(L, p, None, 0, f0, C0)
+    d = orc.detail()
+    assert norm_err(s.get_field(0, L.FIELD_RHO), d["rho"], 1) < 1e-6
+    assert norm_err(s.get_field(0, L.FIELD_U), d["u"], 1) < 1e-5
+
+
+def test_full_size_config2_parity(L):
+    """Full 192 x 96 x 80 lattice of the matrix-viscoelastic workload, in the
+    benchmark's launch configuration: every cell after 3 steps from a
+    perturbed state."""
+    p, rho, _ = configs.config2(0.2)
+    f0, C0 = random_populations((p.Lx, p.Ly, p.Lz), seed=21, amp=0.01)
+    s, orc = run_pair(L, p, rho, 3, f0, C0)
+    assert norm_err(s.get_field(0, L.FIELD_F), orc.f, 2) < TOL_FEW
+    assert tensor_err(s.get_field(0, L.FIELD_C), orc.C) < TOL_FEW
+
+
+def test_observables_match_oracle_on_gpu_state(L):
+    """Droplet observables of the same state: integer decisions (volume,
+    L_p, necks, fragments) exactly equal, D and theta to rounding."""
+    p, rho, _ = configs.config1()
+    s = L.Solver(p)
+    s.init(0, rho)
+    s.step(200)
+    ob = s.observables(0)
+    orc = O.Oracle(p.oracle_dict())
+    orc.f[:] = s.get_field(0, L.FIELD_F)
+    ro = orc.observables(indicator_fp32=True)
+    for k in ("volume", "Lp", "necks", "fragments", "broken"):
+        assert ob[k] == ro[k], k
+    assert abs(ob["D"] - ro["D"]) < 1e-10
+    assert abs(ob["theta_deg"] - ro["theta_deg"]) < 1e-8
+    assert np.allclose(ob["centroid"], ro["centroid"], atol=1e-9)
+    assert np.allclose(ob["mass"], ro["mass"], rtol=1e-6)
+
+
+def test_gpu_mass_conservation_fp32(L):
+    p, rho, _ = configs.config1()
+    s = L.Solver(p)
+    s.init(0, rho)
+    m0 = np.array(s.observables(0)["mass"])
+    s.step(500)
+    m1 = np.array(s.observables(0)["mass"])
+    assert np.all(np.abs(m1 - m0) / m0 < 2e-6)
+
+
+def test_gpu_couette(L):
+    """Single component between walls at -/+ Uw: the linear profile."""
+    Lz, Uw = 16, 0.01
+    p = L.Params(Lx=8, Ly=4, Lz=Lz, Uw=Uw, G=0.0, eta_M=0.5, rho_in=1.0, rho_out=0.0)
+    rho = np.zeros((2, Lz, 4, 8))
+    rho[0] = 1.0
+    s = L.Solver(p)
+    s.init(0, rho)
+    s.step(1500)
+    u = s.get_field(0, L.FIELD_U)
+    z = np.arange(Lz)
+    exact = Uw * (2 * (z + 0.5) / Lz - 1)
+    assert np.abs(u[0, :, 1, 3] - exact).max() < 2e-7
+
+
+def test_divergence_is_flagged_not_faulted(L):
+    """A conformation beyond the extensibility limit (host-injected) makes
+    the step kernel set the device status word; the host sees DIVERGED."""
+    p = L.Params(Lx=8, Ly=8, Lz=8, Uw=0.01, eta_M=0.5, eta_P=0.1, tau_P=5.0, L2=20.0, visco_phase=1)
+    s = L.Solver(p)
+    s.init(0, synth.droplet_densities(8, 8, 8, 2.5, seed=1))
+    assert s.check() == L.OK
+    C = s.get_field(0, L.FIELD_C)
+    C[0, 4, 4, 4] = 30.0
+    s.set_field(0, L.FIELD_C, C)
+    s.step(1)
+    assert s.check() == L.ERR_DIVERGED
+    with pytest.raises(L.LbfeError):
+        s.observables(0)
+
+
+@pytest.mark.parametrize("tile_y,z_chunk", [(4, 0), (8, 8), (16, 0), (8, 5), (16, 3), (4, 13)])
+def test_launch_shapes_agree(L, tile_y, z_chunk):
+    """Every tile height and z-chunk depth of the fused step gives the same
+    fields (ragged box: 40 x 20 x 13 does not divide the 32 x TY tiles)."""
+    shape = (40, 20, 13)
+    p = L.Params(Lx=40, Ly=20, Lz=13, R=3.0, Uw=0.03, G=3.1, eta_M=0.5, eta_P=0.2, tau_P=9.0,
+                 L2=60.0, visco_phase=1)
+    f0, C0 = random_populations(shape, seed=77)
+    ref, orc = run_pair(L, p, None, 3, f0, C0)
+    s = L.Solver(p)
+    s.init(0, np.ones((2, 13, 20, 40)))
+    s.set_field(0, L.FIELD_F, f0)
+    s.set_field(0, L.FIELD_C, C0)
+    s.tune(tile_y, z_chunk)
+    cfg = s.launch_config()
+    assert cfg["tile_y"] == tile_y
+    s.step(3)
+    fg, Cg = s.get_field(0, L.FIELD_F), s.get_field(0, L.FIELD_C)
+    assert np.abs(fg - ref.get_field(0, L.FIELD_F)).max() <= 1e-6
+    assert np.abs(Cg - ref.get_field(0, L.FIELD_C)).max() <= 1e-6
+    assert norm_err(fg, orc.f, 2) < TOL_FEW and tensor_err(Cg, orc.C) < TOL_FEW
+
+
+def test_batch_equals_solo_runs(L):
+    """Instances of uneven size and parameters advanced in one persistent
+    launch give exactly their single-instance results."""
+    ps = [L.Params(Lx=40, Ly=24, Lz=12, R=4.0, Uw=0.02, G=3.1, eta_M=0.6, eta_P=0.24, tau_P=30.0,
+                   visco_phase=1, sigma=0.0592),
+          L.Params(Lx=64, Ly=32, Lz=20, R=6.0, Uw=0.03, G=3.1, eta_M=0.9, eta_P=0.36, tau_P=50.0,
+                   visco_phase=2, lambda_=3.0, sigma=0.0592),
+          L.Params(Lx=24, Ly=16, Lz=10, R=3.0, Uw=0.01, G=3.1, eta_M=0.4, visco_phase=0, sigma=0.0592)]
+    rhos = [synth.droplet_densities(p.Lx, p.Ly, p.Lz, p.R, seed=30 + k) for k, p in enumerate(ps)]
+    batch = L.Solver(ps)
+    for k, r in enumerate(rhos):
+        batch.init(k, r)
+    batch.step(25)
+    for k, (p, r) in enumerate(zip(ps, rhos)):
+        solo = L.Solver(p)
+        solo.init(0, r)
+        solo.step(25)
+        assert np.array_equal(batch.get_field(k, L.FIELD_F), solo.get_field(0, L.FIELD_F)), k
+        assert np.array_equal(batch.get_field(k, L.FIELD_C), solo.get_field(0, L.FIELD_C)), k
+        ob, os_ = batch.observables(k), solo.observables(0)
+        assert ob["D"] == os_["D"] and ob["volume"] == os_["volume"]
