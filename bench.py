@@ -266,7 +266,7 @@ def run_ours(a):
     algo = ALGO_BYTES[prec]
     achieved = algo * p.N / (ms_per_step / 1e3) / 1e9
     traffic_per_lup, prof_file = profiled_traffic(a.workload, prec)
-    roof = {"bound": "hbm", "kernel": "step (moments + forces + update kernels)",
+    roof = {"bound": "hbm", "kernel": "k_fused (whole time step in one kernel)",
             "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "algorithmic_bytes_per_lup": algo,
             "traffic": (round(traffic_per_lup * p.N) if traffic_per_lup else None),

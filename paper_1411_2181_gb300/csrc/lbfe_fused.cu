@@ -37,8 +37,8 @@ struct Geom {
     static constexpr int R2N = RX * RY;
     static constexpr int NHALO = R2N - NT;             // radius-2 cells outside the tile
     static constexpr int NRING1 = 2 * (RX - 2) + 2 * TY;  // radius-1 cells outside the tile
-    // rings: rho (float2) x3, Pi 6x3, j 3x2, C 6x4, u 3x3
-    static constexpr int FLOATS = (2 * 3 + 18 + 6 + 24 + 9) * R2N;
+    // rings: rho (float2) x3, stress scalars (a f, a) x3, j 3x2, C 6x4, u 3x3
+    static constexpr int FLOATS = (2 * 3 + 2 * 3 + 6 + 24 + 9) * R2N;
 };
 
 __device__ __forceinline__ int ring3(int p) { return (p + 12) % 3; }
@@ -91,75 +91,102 @@ __device__ __forceinline__ void ring1_coord(int h, int &gx, int &gy) {
     }
 }
 
-struct Rings {
-    float2 *rho;   // [3][R2N]
-    float *pi;     // [3][6][R2N]
-    float *j;      // [2][3][R2N]
-    float *c;      // [4][6][R2N]
-    float *u;      // [3][3][R2N]
+typedef unsigned int u32;
+
+// Shared-memory rings (offsets in floats from the dynamic shared base):
+//   rho  float2 [3][R2N]          densities rho_A, rho_B
+//   pi   float  [3][2][R2N]       a f and a of Pi = a (f C) - a I, a = (eta_P/tau_P) chi
+//   j    float  [2][3][R2N]       momentum
+//   c    float  [4][6][R2N]       conformation
+//   u    float  [3][3][R2N]       velocity
+template <int TY>
+struct Ring {
+    static constexpr int R2N = Geom<TY>::R2N;
+    static constexpr int RHO = 0, PI = 6 * R2N, J = PI + 6 * R2N, C = J + 6 * R2N, U = C + 24 * R2N;
 };
 
-// Stage M for one cell: moments, stress and conformation into the rings.
-template <typename T, int TY>
-__device__ __forceinline__ void stage_m_cell(const InstDev &I, const T *__restrict__ fin,
-                                             const float *__restrict__ Cin, long long n, int idx,
-                                             const Rings &R, int p) {
-    constexpr int R2N = Geom<TY>::R2N;
-    const long long S = I.S;
+extern __shared__ float4 lbfe_smem4[];
+__device__ __forceinline__ float *smem() { return reinterpret_cast<float *>(lbfe_smem4); }
+
+// Stage M inputs of one cell: its 38 populations and 6 conformation components.
+struct MCell {
+    float f[2 * Q];
+    float c[6];
+};
+
+// Cell offsets are 32-bit: an instance holds at most 2^26 cells, so every
+// field offset (s*19 + i)*S + n stays below 2^32.
+template <typename T>
+__device__ __forceinline__ void m_load(const InstDev &I, const T *__restrict__ fin, const float *__restrict__ Cin,
+                                       u32 S, u32 n, MCell &m) {
     const float ra0 = I.rho0[0], rb0 = I.rho0[1];
-    float fa[Q], fb[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        fa[i] = ldpop(fin + (long long)i * S + n, wq(i) * ra0);
-        fb[i] = ldpop(fin + (long long)(Q + i) * S + n, wq(i) * rb0);
+        m.f[i] = ldpop(fin + (u32)(i * S + n), wq(i) * ra0);
+        m.f[Q + i] = ldpop(fin + (u32)((Q + i) * S + n), wq(i) * rb0);
     }
-    float c[6];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) c[k] = __ldg(Cin + (long long)k * S + n);
+    for (int k = 0; k < 6; ++k) m.c[k] = __ldg(Cin + (u32)(k * S + n));
+}
+
+// Stage M for one cell: moments, stress scalars and conformation into the
+// ring slots of its plane.
+template <int TY>
+__device__ __forceinline__ void m_store(const InstDev &I, const MCell &m, int idx, int s3, int s2, int s4) {
+    constexpr int R2N = Geom<TY>::R2N;
+    using Rg = Ring<TY>;
+    float2 *rho_s = reinterpret_cast<float2 *>(smem() + Rg::RHO) + s3 * R2N;
+    float *pi_s = smem() + Rg::PI + s3 * 2 * R2N;
+    float *j_s = smem() + Rg::J + s2 * 3 * R2N;
+    float *c_s = smem() + Rg::C + s4 * 6 * R2N;
     float rA = 0.f, rB = 0.f;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) { rA += fa[i]; rB += fb[i]; }
+    for (int i = 0; i < Q; ++i) { rA += m.f[i]; rB += m.f[Q + i]; }
     // momentum from opposite-pair differences (exact in FP32 per pair)
     float jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {
-        const float d = (fa[i] - fa[i + 1]) + (fb[i] - fb[i + 1]);
+        const float d = (m.f[i] - m.f[i + 1]) + (m.f[Q + i] - m.f[Q + i + 1]);
         if (cx(i)) jx += cx(i) * d;
         if (cy(i)) jy += cy(i) * d;
         if (cz(i)) jz += cz(i) * d;
     }
-    const int s3 = ring3(p), s2 = ring2(p), s4 = ring4(p);
-    R.rho[s3 * R2N + idx] = make_float2(rA, rB);
-    float *jr = R.j + s2 * 3 * R2N;
-    jr[idx] = jx;
-    jr[R2N + idx] = jy;
-    jr[2 * R2N + idx] = jz;
-    float *cr = R.c + s4 * 6 * R2N;
+    rho_s[idx] = make_float2(rA, rB);
+    j_s[idx] = jx;
+    j_s[R2N + idx] = jy;
+    j_s[2 * R2N + idx] = jz;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) cr[k * R2N + idx] = c[k];
+    for (int k = 0; k < 6; ++k) c_s[k * R2N + idx] = m.c[k];
     float a = 0.f, fp = 1.f;
     if (I.visc_comp >= 0) {
         a = I.pi_coef * (I.visc_comp == 0 ? rA : rB) / (rA + rB);
-        fp = peterlin(I.L2, c[0], c[1], c[2]);
+        fp = peterlin(I.L2, m.c[0], m.c[1], m.c[2]);
     }
-    float *pr = R.pi + s3 * 6 * R2N;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) pr[k * R2N + idx] = a * (fp * c[k] - (k < 3 ? 1.f : 0.f));
+    pi_s[idx] = a * fp;
+    pi_s[R2N + idx] = a;
 }
 
-// Stage F for one cell of plane q: forces and velocity.  Writes u to the
-// ring; returns the per-component total forces, u and the densities.
+// Ring slots of the planes one iteration touches (q = p - 1, r = p - 2).
+struct Slots {
+    int r3[3];   // rho / pi / u slots of planes q-1, q, q+1 (plane r-1 = q-2 shares q+1's slot)
+    int c4[4];   // C slots of planes q-2, q-1, q, q+1
+    int j2;      // j slot of plane q
+};
+
+// Stage F for one cell of plane q: Shan-Chen and polymer forces and the
+// velocity.  Writes u to the ring; returns the per-component total forces,
+// u and the densities.
 template <int TY>
-__device__ __forceinline__ void stage_f_cell(const InstDev &I, int idx, const Rings &R, int q,
-                                             float FA[3], float FB[3], float u[3], float &rA, float &rB) {
+__device__ __forceinline__ void stage_f_cell(const InstDev &I, int idx, const Slots &L, float FA[3], float FB[3],
+                                             float u[3], float &rA, float &rB) {
     constexpr int R2N = Geom<TY>::R2N, RX = Geom<TY>::RX;
-    const float2 *rm = R.rho + ring3(q - 1) * R2N;
-    const float2 *rc = R.rho + ring3(q) * R2N;
-    const float2 *rp = R.rho + ring3(q + 1) * R2N;
+    using Rg = Ring<TY>;
+    const float2 *rho0 = reinterpret_cast<const float2 *>(smem() + Rg::RHO);
+    const float2 *rm = rho0 + L.r3[0] * R2N, *rc = rho0 + L.r3[1] * R2N, *rp = rho0 + L.r3[2] * R2N;
     const float2 r0 = rc[idx];
     rA = r0.x;
     rB = r0.y;
-    // Shan-Chen with opposite neighbours in pairs
+    // Shan-Chen with opposite neighbours in pairs: w_i c_i (rho(x + c_i) - rho(x - c_i))
     float sA[3] = {0.f, 0.f, 0.f}, sB[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {
@@ -171,30 +198,86 @@ __device__ __forceinline__ void stage_f_cell(const InstDev &I, int idx, const Ri
         if (cy(i)) { sA[1] += cy(i) * w * dB; sB[1] += cy(i) * w * dA; }
         if (cz(i)) { sA[2] += cz(i) * w * dB; sB[2] += cz(i) * w * dA; }
     }
-    // polymer force F_P,a = sum_b (Pi_ba(x + e_b) - Pi_ba(x - e_b))/2
+    // polymer force F_P,a = sum_b (Pi_ba(x + e_b) - Pi_ba(x - e_b))/2 with
+    // Pi_ba = (a f) C_ba - a delta_ba
     float FP[3] = {0.f, 0.f, 0.f};
     if (I.visc_comp >= 0) {
-        const float *pm = R.pi + ring3(q - 1) * 6 * R2N;
-        const float *pc = R.pi + ring3(q) * 6 * R2N;
-        const float *pp = R.pi + ring3(q + 1) * 6 * R2N;
+        const float *sm_ = smem() + Rg::PI + L.r3[0] * 2 * R2N;
+        const float *sc_ = smem() + Rg::PI + L.r3[1] * 2 * R2N;
+        const float *sp_ = smem() + Rg::PI + L.r3[2] * 2 * R2N;
+        const float *cm = smem() + Rg::C + L.c4[1] * 6 * R2N;
+        const float *cc = smem() + Rg::C + L.c4[2] * 6 * R2N;
+        const float *cp = smem() + Rg::C + L.c4[3] * 6 * R2N;
+        const float afxp = sc_[idx + 1], afxm = sc_[idx - 1], afyp = sc_[idx + RX], afym = sc_[idx - RX];
+        const float afzp = sp_[idx], afzm = sm_[idx];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const float gxd = pc[symk(0, a) * R2N + idx + 1] - pc[symk(0, a) * R2N + idx - 1];
-            const float gyd = pc[symk(1, a) * R2N + idx + RX] - pc[symk(1, a) * R2N + idx - RX];
-            const float gzd = pp[symk(2, a) * R2N + idx] - pm[symk(2, a) * R2N + idx];
+            float gxd = afxp * cc[symk(0, a) * R2N + idx + 1] - afxm * cc[symk(0, a) * R2N + idx - 1];
+            float gyd = afyp * cc[symk(1, a) * R2N + idx + RX] - afym * cc[symk(1, a) * R2N + idx - RX];
+            float gzd = afzp * cp[symk(2, a) * R2N + idx] - afzm * cm[symk(2, a) * R2N + idx];
+            if (a == 0) gxd -= sc_[R2N + idx + 1] - sc_[R2N + idx - 1];
+            if (a == 1) gyd -= sc_[R2N + idx + RX] - sc_[R2N + idx - RX];
+            if (a == 2) gzd -= sp_[R2N + idx] - sm_[R2N + idx];
             FP[a] = 0.5f * (gxd + gyd + gzd);
         }
     }
-    const float *jr = R.j + ring2(q) * 3 * R2N;
     const float g[3] = {I.gx, I.gy, I.gz};
     const float inv = 1.0f / (rA + rB);
-    float *ur = R.u + ring3(q) * 3 * R2N;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         FA[a] = -I.G * rA * sA[a] + (rA * inv) * FP[a] + rA * g[a];
         FB[a] = -I.G * rB * sB[a] + (rB * inv) * FP[a] + rB * g[a];
-        u[a] = (jr[a * R2N + idx] + 0.5f * (FA[a] + FB[a])) * inv;
-        ur[a * R2N + idx] = u[a];
+        u[a] = (smem()[Rg::J + L.j2 * 3 * R2N + a * R2N + idx] + 0.5f * (FA[a] + FB[a])) * inv;
+        smem()[Rg::U + L.r3[1] * 3 * R2N + a * R2N + idx] = u[a];
+    }
+}
+
+// Store post-collision population d of the cell at offset n into its
+// streamed position x + c_d.  With WALLS, a population whose target lies
+// beyond a wall returns into the cell as the opposite direction (halfway
+// bounce-back) with the moving-wall term -6 w_d rho_s (c_d . U_wall).
+template <typename T, bool WALLS>
+__device__ __forceinline__ void push_one(T *__restrict__ fdst, u32 S, int s, int d, float v, float rs, float r0s,
+                                         u32 n, bool bottom, bool top, float Uw, int LxLy, const int dxy[3][3]) {
+    int dir = d;
+    u32 dst = n + (u32)(cz(d) * LxLy + dxy[cx(d) + 1][cy(d) + 1]);
+    if (WALLS && ((cz(d) < 0 && bottom) || (cz(d) > 0 && top))) {
+        v -= 6.f * wq(d) * rs * (float)cx(d) * (cz(d) < 0 ? -Uw : Uw);
+        dir = opp(d);
+        dst = n;
+    }
+    if (Store<T>::offset) v -= wq(d) * r0s;
+    Store<T>::st(fdst + (u32)((s * Q + dir) * S + dst), v);
+}
+
+// BGK + Guo collision of one component at one cell and push streaming of
+// its 19 populations.  Opposite directions share the symmetric parts:
+//   f^eq_{i,-i} = w rho (1 + 9/2 (c.u)^2 - 3/2 u.u) +- 3 w rho (c.u)
+//   S_{i,-i}    = (1 - 1/2tau) w (9 (c.u)(c.F) - 3 u.F) +- 3 (1 - 1/2tau) w (c.F)
+template <typename T, bool WALLS>
+__device__ __forceinline__ void collide_push(const float *fv, T *__restrict__ fdst, u32 S, int s, float rs, float r0s,
+                                             const float u[3], const float F[3], float om, u32 n, bool bottom,
+                                             bool top, float Uw, int LxLy, const int dxy[3][3]) {
+    const float omc = 1.0f - om, pref = 1.0f - 0.5f * om;
+    const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const float uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+    const float base0 = rs * (1.f - 1.5f * uu);   // rho (1 - 3/2 u.u)
+    const float srcb = -3.f * uF * pref;           // (1 - 1/2tau)(-3 u.F)
+    {
+        float v = omc * fv[0] + wq(0) * (om * base0 + srcb);
+        if (Store<T>::offset) v -= wq(0) * r0s;
+        Store<T>::st(fdst + (u32)(s * Q * S + n), v);
+    }
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const float w = wq(i);
+        const float cu = cx(i) * u[0] + cy(i) * u[1] + cz(i) * u[2];
+        const float cF = cx(i) * F[0] + cy(i) * F[1] + cz(i) * F[2];
+        const float sym = w * (om * (base0 + 4.5f * rs * cu * cu) + srcb + 9.f * pref * cu * cF);
+        const float anti = w * (om * 3.f * rs * cu + 3.f * pref * cF);
+        push_one<T, WALLS>(fdst, S, s, i, omc * fv[i] + (sym + anti), rs, r0s, n, bottom, top, Uw, LxLy, dxy);
+        push_one<T, WALLS>(fdst, S, s, i + 1, omc * fv[i + 1] + (sym - anti), rs, r0s, n, bottom, top, Uw, LxLy,
+                           dxy);
     }
 }
 
@@ -205,24 +288,21 @@ __global__ void __launch_bounds__(32 * TY, TY >= 16 ? 1 : (TY >= 8 ? 2 : 3))
 k_fused(const InstDev *__restrict__ insts, const int *__restrict__ item_off, int n_inst, int total_items,
         int cur, unsigned *status) {
     using Gm = Geom<TY>;
-    constexpr int TX = Gm::TX, NT = Gm::NT, RX = Gm::RX, R2N = Gm::R2N;
-    extern __shared__ float4 smem4[];
-    float *sm = reinterpret_cast<float *>(smem4);
-    Rings R;
-    R.rho = reinterpret_cast<float2 *>(sm);
-    R.pi = sm + 6 * R2N;
-    R.j = R.pi + 18 * R2N;
-    R.c = R.j + 6 * R2N;
-    R.u = R.c + 24 * R2N;
+    constexpr int TX = Gm::TX, NT = Gm::NT, RX = Gm::RX, RY = Gm::RY, R2N = Gm::R2N;
+    constexpr int MR = (R2N + NT - 1) / NT;   // stage-M rounds per thread
+    using Rg = Ring<TY>;
+    __shared__ u32 s_rows[RY];   // in-plane offsets of the radius-2 rows (wrapped)
+    __shared__ u32 s_cols[RX];   // x of the radius-2 columns (wrapped)
 
     const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
-    const int gxi = tx + 2, gyi = ty + 2, idx_in = gyi * RX + gxi;
+    const int idx_in = (ty + 2) * RX + (tx + 2);
 
     for (int item = blockIdx.x; item < total_items; item += gridDim.x) {
         const int k = find_inst(item_off, n_inst, item);
         const InstDev &I = insts[k];
         const int Lx = I.Lx, Ly = I.Ly, Lz = I.Lz;
-        const long long LxLy = (long long)Lx * Ly, S = I.S;
+        const int LxLy = Lx * Ly;
+        const u32 S = (u32)I.S;
         int local = item - __ldg(item_off + k);
         const int bx = local % I.ntx;
         local /= I.ntx;
@@ -234,106 +314,104 @@ k_fused(const InstDev *__restrict__ insts, const int *__restrict__ item_off, int
         T *__restrict__ fout = (T *)I.f[cur ^ 1];
         const float *__restrict__ Cin = I.C[cur];
         float *__restrict__ Cout = I.C[cur ^ 1];
+        const float Uw = I.Uw;
 
-        // own cell and its periodic neighbours
+        __syncthreads();  // previous item done with the row/column tables
+        if (t < RY) s_rows[t] = (u32)(wrapg(y0 + t, Ly) * Lx);
+        if (t < RX) s_cols[t] = (u32)wrapg(x0 + t, Lx);
+        __syncthreads();
+
+        // own cell and the offsets of its 3 x 3 in-plane neighbourhood
         const int x = bx * TX + tx, y = by * TY + ty;
         const bool valid = x < Lx && y < Ly;
-        const long long ofs_in = (long long)wrapg(y, Ly) * Lx + wrapg(x, Lx);
-        const int xm = wrapg(x - 1, Lx), xp = wrapg(x + 1, Lx);
-        const long long rowm = (long long)wrapg(y - 1, Ly) * Lx, row0 = (long long)wrapg(y, Ly) * Lx,
-                        rowp = (long long)wrapg(y + 1, Ly) * Lx;
-        const int xw = wrapg(x, Lx);
+        const u32 ofs_in = s_rows[ty + 2] + s_cols[tx + 2];
+        int dxy[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) dxy[a][b] = (int)(s_rows[ty + 1 + b] + s_cols[tx + 1 + a]) - (int)ofs_in;
+        // in-plane offsets of this thread's stage-M cells (i = t + r NT)
+        u32 om_ofs[MR];
+#pragma unroll
+        for (int r = 0; r < MR; ++r) {
+            const int i = min(t + r * NT, R2N - 1), gy = i / RX;
+            om_ofs[r] = s_rows[gy] + s_cols[i - gy * RX];
+        }
 
         float FA[3], FB[3], uo[3], rAo = 1.f, rBo = 0.f;
 
         for (int p = z0 - 2; p <= z1 + 1; ++p) {
+            const int q = p - 1, r = p - 2;
+            Slots L;
+            L.r3[0] = ring3(q - 1);
+            L.r3[1] = ring3(q);
+            L.r3[2] = ring3(q + 1);
+            L.c4[0] = ring4(q - 2);
+            L.c4[1] = ring4(q - 1);
+            L.c4[2] = ring4(q);
+            L.c4[3] = ring4(q + 1);
+            L.j2 = ring2(q);
+
             // ---------------- stage M(p): radius-2 region of plane clamp(p)
             {
-                const long long pl = (long long)min(max(p, 0), Lz - 1) * LxLy;
-                stage_m_cell<T, TY>(I, fin, Cin, pl + ofs_in, idx_in, R, p);
-                for (int h = t; h < Gm::NHALO; h += NT) {
-                    int gx, gy;
-                    halo2_coord<TY>(h, gx, gy);
-                    const long long o = (long long)wrapg(y0 + gy, Ly) * Lx + wrapg(x0 + gx, Lx);
-                    stage_m_cell<T, TY>(I, fin, Cin, pl + o, gy * RX + gx, R, p);
+                const u32 pl = (u32)(min(max(p, 0), Lz - 1) * LxLy);
+#pragma unroll
+                for (int rr = 0; rr < MR; ++rr) {
+                    const int i = t + rr * NT;
+                    if (rr * NT + NT <= R2N || i < R2N) {
+                        MCell m;
+                        m_load<T>(I, fin, Cin, S, pl + om_ofs[rr], m);
+                        m_store<TY>(I, m, i, L.r3[2], ring2(p), L.c4[3]);
+                    }
                 }
             }
             __syncthreads();
             // ---------------- stage F(q): radius-1 region
-            const int q = p - 1;
-            const bool doF = q >= max(z0 - 1, 0) && q <= min(z1, Lz - 1);
-            if (doF) {
-                stage_f_cell<TY>(I, idx_in, R, q, FA, FB, uo, rAo, rBo);
+            if (q >= max(z0 - 1, 0) && q <= min(z1, Lz - 1)) {
+                stage_f_cell<TY>(I, idx_in, L, FA, FB, uo, rAo, rBo);
                 for (int h = t; h < Gm::NRING1; h += NT) {
                     int gx, gy;
                     ring1_coord<TY>(h, gx, gy);
                     float a[3], b[3], uu[3], ra, rb;
-                    stage_f_cell<TY>(I, gy * RX + gx, R, q, a, b, uu, ra, rb);
+                    stage_f_cell<TY>(I, gy * RX + gx, L, a, b, uu, ra, rb);
                 }
             }
             __syncthreads();
             // ---------------- stage X(q): collision + push streaming
             if (q >= z0 && q < z1 && valid) {
+                const u32 nq = (u32)(q * LxLy) + ofs_in;
+                float fx[2 * Q];
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    fx[i] = ldpop(fin + (long long)i * S + nq, wq(i) * I.rho0[0]);
+                    fx[Q + i] = ldpop(fin + (long long)(Q + i) * S + nq, wq(i) * I.rho0[1]);
+                }
                 const float rt = rAo + rBo;
                 if (!(rt > 0.f) || uo[0] != uo[0] || uo[1] != uo[1] || uo[2] != uo[2])
                     atomicOr(status, kFlagDiverged);
                 const float nu = (rAo * I.nu_A + rBo * I.nu_B) / rt;
                 const float om = 1.0f / (3.0f * nu + 0.5f);
-                const float pref = 1.0f - 0.5f * om;
-                const float uu = uo[0] * uo[0] + uo[1] * uo[1] + uo[2] * uo[2];
-                const long long n = (long long)q * LxLy + ofs_in;
-#pragma unroll
-                for (int s = 0; s < 2; ++s) {
-                    const float rs = s == 0 ? rAo : rBo;
-                    const float r0s = I.rho0[s];
-                    const float Fx = s == 0 ? FA[0] : FB[0], Fy = s == 0 ? FA[1] : FB[1],
-                                Fz = s == 0 ? FA[2] : FB[2];
-                    const float uF = uo[0] * Fx + uo[1] * Fy + uo[2] * Fz;
-                    float fv[Q];
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) fv[i] = ldpop(fin + (long long)(s * Q + i) * S + n, wq(i) * r0s);
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) {
-                        const float cu = cx(i) * uo[0] + cy(i) * uo[1] + cz(i) * uo[2];
-                        const float cF = cx(i) * Fx + cy(i) * Fy + cz(i) * Fz;
-                        const float feq = wq(i) * rs * (1.f + 3.f * cu + 4.5f * cu * cu - 1.5f * uu);
-                        const float src = pref * wq(i) * (3.f * (cF - uF) + 9.f * cu * cF);
-                        float v = fv[i] - om * (fv[i] - feq) + src;
-                        const int zd = q + cz(i);
-                        int dir = i;
-                        long long dst;
-                        if (zd < 0 || zd >= Lz) {
-                            // halfway bounce-back, moving-wall term -6 w_i rho_s (c_i . U_wall)
-                            const float uw = zd < 0 ? -I.Uw : I.Uw;
-                            v -= 6.f * wq(i) * rs * (float)cx(i) * uw;
-                            dir = opp(i);
-                            dst = n;
-                        } else {
-                            const long long row = cy(i) > 0 ? rowp : (cy(i) < 0 ? rowm : row0);
-                            const int col = cx(i) > 0 ? xp : (cx(i) < 0 ? xm : xw);
-                            dst = (long long)zd * LxLy + row + col;
-                        }
-                        if (Store<T>::offset) v -= wq(i) * r0s;
-                        Store<T>::st(fout + (long long)(s * Q + dir) * S + dst, v);
-                    }
-                }
+                const bool bottom = q == 0, top = q == Lz - 1;
+                collide_push<T, true>(fx, fout, S, 0, rAo, I.rho0[0], uo, FA, om, nq, bottom, top, Uw, LxLy, dxy);
+                collide_push<T, true>(fx + Q, fout, S, 1, rBo, I.rho0[1], uo, FB, om, nq, bottom, top, Uw, LxLy, dxy);
             }
-            // ---------------- stage U(r): FENE-P update
-            const int r = p - 2;
+            // ---------------- stage U(r): FENE-P update, Eq. 2 (Eq. 4)
             if (r >= z0 && r < z1 && valid) {
-                const float *um = R.u + ring3(r - 1) * 3 * R2N;
-                const float *uc = R.u + ring3(r) * 3 * R2N;
-                const float *up = R.u + ring3(r + 1) * 3 * R2N;
-                const float *cm = R.c + ring4(r - 1) * 6 * R2N;
-                const float *cc = R.c + ring4(r) * 6 * R2N;
-                const float *cp = R.c + ring4(r + 1) * 6 * R2N;
+                // planes r-1, r, r+1 = q-2, q-1, q: u slots r3[2], r3[0], r3[1]
+                const float *um = smem() + Rg::U + L.r3[2] * 3 * R2N;
+                const float *uc = smem() + Rg::U + L.r3[0] * 3 * R2N;
+                const float *up = smem() + Rg::U + L.r3[1] * 3 * R2N;
+                const float *cm = smem() + Rg::C + L.c4[0] * 6 * R2N;
+                const float *cc = smem() + Rg::C + L.c4[1] * 6 * R2N;
+                const float *cp = smem() + Rg::C + L.c4[2] * 6 * R2N;
                 const int i0 = idx_in;
                 float u0[3], Gr[3][3];
 #pragma unroll
                 for (int j = 0; j < 3; ++j) u0[j] = uc[j * R2N + i0];
+                // grad u by central differences, u_ghost = 2 U_wall - u at the walls
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
-                    const float uwb = j == 0 ? -I.Uw : 0.f, uwt = j == 0 ? I.Uw : 0.f;
+                    const float uwb = j == 0 ? -Uw : 0.f, uwt = j == 0 ? Uw : 0.f;
                     const float uzp = (r == Lz - 1) ? 2.f * uwt - u0[j] : up[j * R2N + i0];
                     const float uzm = (r == 0) ? 2.f * uwb - u0[j] : um[j * R2N + i0];
                     Gr[0][j] = 0.5f * (uc[j * R2N + i0 + 1] - uc[j * R2N + i0 - 1]);
@@ -343,18 +421,19 @@ k_fused(const InstDev *__restrict__ insts, const int *__restrict__ item_off, int
                 float c[6];
 #pragma unroll
                 for (int q6 = 0; q6 < 6; ++q6) c[q6] = cc[q6 * R2N + i0];
+                // first-order upwind u . grad C (C mirrored at the walls)
+                const int ox = u0[0] > 0.f ? -1 : 1, oy = u0[1] > 0.f ? -RX : RX;
+                const float sx = u0[0] > 0.f ? u0[0] : -u0[0], sy = u0[1] > 0.f ? u0[1] : -u0[1];
+                const float sz = u0[2] > 0.f ? u0[2] : -u0[2];
+                const float *cz_ = u0[2] > 0.f ? cm : cp;
                 float adv[6];
 #pragma unroll
-                for (int q6 = 0; q6 < 6; ++q6) {
-                    const float *col = cc + q6 * R2N;
-                    const float ax = u0[0] > 0.f ? (c[q6] - col[i0 - 1]) : (col[i0 + 1] - c[q6]);
-                    const float ay = u0[1] > 0.f ? (c[q6] - col[i0 - RX]) : (col[i0 + RX] - c[q6]);
-                    const float az = u0[2] > 0.f ? (c[q6] - cm[q6 * R2N + i0]) : (cp[q6 * R2N + i0] - c[q6]);
-                    adv[q6] = u0[0] * ax + u0[1] * ay + u0[2] * az;
-                }
+                for (int q6 = 0; q6 < 6; ++q6)
+                    adv[q6] = sx * (c[q6] - cc[q6 * R2N + i0 + ox]) + sy * (c[q6] - cc[q6 * R2N + i0 + oy]) +
+                              sz * (c[q6] - cz_[q6 * R2N + i0]);
                 const float Cm[3][3] = {{c[0], c[3], c[4]}, {c[3], c[1], c[5]}, {c[4], c[5], c[2]}};
                 const float fp = peterlin(I.L2, c[0], c[1], c[2]);
-                const long long n = (long long)r * LxLy + ofs_in;
+                const u32 n = (u32)(r * LxLy) + ofs_in;
 #pragma unroll
                 for (int q6 = 0; q6 < 6; ++q6) {
                     const int a = q6 < 3 ? q6 : (q6 == 5 ? 1 : 0);
@@ -363,7 +442,7 @@ k_fused(const InstDev *__restrict__ insts, const int *__restrict__ item_off, int
 #pragma unroll
                     for (int m = 0; m < 3; ++m) st += Cm[a][m] * Gr[m][b] + Gr[m][a] * Cm[m][b];
                     const float relax = (fp * c[q6] - (q6 < 3 ? 1.f : 0.f)) * I.inv_tauP;
-                    Cout[(long long)q6 * S + n] = c[q6] + (-adv[q6] + st - relax);
+                    Cout[(u32)(q6 * S + n)] = c[q6] + (-adv[q6] + st - relax);
                 }
                 if (!(c[0] + c[1] + c[2] < I.L2)) atomicOr(status, kFlagDiverged);
             }
