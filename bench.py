@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="matrix_ve_192x96x80",
-                    choices=["matrix_ve_192x96x80", "droplet_ve_256x128x64", "box_32cubed"])
+                    choices=["matrix_ve_192x96x80", "droplet_ve_256x128x64", "box_32cubed", "batched_64"])
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--precision", choices=["fp32", "fp16", "bf16"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -54,19 +55,31 @@ def parse():
 
 
 def workload(name: str, precision: int):
+    """Instances (list of Params) and their initial densities."""
     from dataclasses import replace
     from paper_1411_2181_gb300 import configs
+    if name == "batched_64":
+        inst = configs.config4(64, seed=4)
+        return ([replace(p, precision=precision) for p, _ in inst],
+                [configs.config4_densities(p, sd) for p, sd in inst])
     if name == "matrix_ve_192x96x80":
         p, rho, _ = configs.config2(0.2)
     elif name == "droplet_ve_256x128x64":
         p, rho, _ = configs.config3()
     else:
         p, rho, _ = configs.config1()
-    return replace(p, precision=precision), rho
+    return [replace(p, precision=precision)], [rho]
 
 
-def config_dict(name, p):
-    return {"workload": name, "lattice": [p.Lx, p.Ly, p.Lz], "cells": p.N, "W": p.Lz, "R": p.R,
+def config_dict(name, ps):
+    cells = sum(p.N for p in ps)
+    if len(ps) > 1:
+        return {"workload": name, "instances": len(ps), "cells": cells,
+                "Lx_range": [min(p.Lx for p in ps), max(p.Lx for p in ps)],
+                "W_range": [min(p.Lz for p in ps), max(p.Lz for p in ps)],
+                "l2_policy": "state (>20 GB) larger than L2; no flush"}
+    p = ps[0]
+    return {"workload": name, "lattice": [p.Lx, p.Ly, p.Lz], "cells": cells, "W": p.Lz, "R": p.R,
             "visco_phase": ["newtonian", "droplet", "matrix"][p.visco_phase], "lambda": p.lambda_,
             "L2": p.L2, "Uw": p.Uw, "l2_policy": "state (>0.5 GB) larger than L2; no flush"}
 
@@ -204,13 +217,20 @@ def run_ours(a):
         build.build()
     if dist:
         tdist.barrier()
-    from paper_1411_2181_gb300 import lbfe
+    from paper_1411_2181_gb300 import lbfe, autotune
     prec = {"fp32": 0, "fp16": 1, "bf16": 2}[a.precision]
-    p, rho = workload(a.workload, prec)
+    ps, rhos = workload(a.workload, prec)
+    ncell = sum(p.N for p in ps)
+    shape = None
+    if not a.no_autotune:
+        shape = autotune.tune(ps, device=f"cuda:{local}", rho=rhos)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        s = lbfe.Solver(p, device=f"cuda:{local}", stream=stream)
-        s.init(0, rho)
+        s = lbfe.Solver(ps, device=f"cuda:{local}", stream=stream)
+        if shape:
+            s.tune(shape["tile_y"], shape["z_chunk"])
+        for k, r in enumerate(rhos):
+            s.init(k, r)
         for _ in range(a.warmup):
             s.step(1)
         torch.cuda.synchronize()
@@ -229,59 +249,64 @@ def run_ours(a):
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1)
         st = s.check()
+        launch = s.launch_config()
     t_max = ms
     if dist:
         tt = torch.tensor([ms], device=f"cuda:{local}")
         tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
         t_max = float(tt.item())
     ms_per_step = t_max / a.steps
-    mlups_rank = p.N * a.steps / (t_max / 1e3) / 1e6
+    mlups_rank = ncell * a.steps / (t_max / 1e3) / 1e6
     value = mlups_rank * world
 
     # end to end through the C ABI: H2D of the initial densities from pinned
     # memory, the steps, and the observables read back, all timed
     e2e = None
     if not a.no_e2e:
-        host = torch.from_numpy(np.ascontiguousarray(rho, dtype=np.float64)).pin_memory()
+        hosts = [torch.from_numpy(np.ascontiguousarray(r, dtype=np.float64)).pin_memory() for r in rhos]
         with torch.cuda.stream(stream):
-            s2 = lbfe.Solver(p, device=f"cuda:{local}", stream=stream)
-            s2.init_from_host_ptr(0, host.data_ptr())
+            s2 = lbfe.Solver(ps, device=f"cuda:{local}", stream=stream)
+            if shape:
+                s2.tune(shape["tile_y"], shape["z_chunk"])
+            for k, hbuf in enumerate(hosts):
+                s2.init_from_host_ptr(k, hbuf.data_ptr())
             s2.step(2)
-            s2.observables(0)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            s2.init_from_host_ptr(0, host.data_ptr())
+            for k, hbuf in enumerate(hosts):
+                s2.init_from_host_ptr(k, hbuf.data_ptr())
             s2.step(a.steps)
-            ob = s2.observables(0)
+            for k in range(len(ps)):
+                s2.observables(k)
             t1 = time.perf_counter()
-        e2e_mlups = p.N * a.steps / (t1 - t0) / 1e6 * world
-        obs_bytes = 6 * p.Lx * 8 + 2 * 8 + 4
+            s2.close()
+        e2e_mlups = ncell * a.steps / (t1 - t0) / 1e6 * world
+        obs_bytes = sum(6 * p.Lx * 8 + 2 * 8 + 4 for p in ps)
         e2e = {"value": round(e2e_mlups, 2), "unit": METRIC,
-               "h2d_bytes_per_step": int(host.numel() * 8 / a.steps),
+               "h2d_bytes_per_step": int(sum(h.numel() for h in hosts) * 8 / a.steps),
                "d2h_bytes_per_step": int(obs_bytes / a.steps),
                "timed": "lbfe_init (pinned H2D of rho[2][N] float64) + lbfe_step(K) + lbfe_observables"}
-        del s2
 
     peak, peak_kind = measured_peak()
     algo = ALGO_BYTES[prec]
-    achieved = algo * p.N / (ms_per_step / 1e3) / 1e9
+    achieved = algo * ncell / (ms_per_step / 1e3) / 1e9
     traffic_per_lup, prof_file = profiled_traffic(a.workload, prec)
     roof = {"bound": "hbm", "kernel": "k_fused (whole time step in one kernel)",
             "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "algorithmic_bytes_per_lup": algo,
-            "traffic": (round(traffic_per_lup * p.N) if traffic_per_lup else None),
+            "traffic": (round(traffic_per_lup * ncell) if traffic_per_lup else None),
             "traffic_source": os.path.relpath(prof_file, ROOT) if (prof_file and traffic_per_lup) else None}
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        cpu = oracle_sample(p, rho)
+        cpu = oracle_sample(ps[0], rhos[0])
 
     if rank == 0:
         out = {"metric": METRIC, "value": round(value, 2), "unit": METRIC, "n_gpus": world,
                "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms_per_step, 5),
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": DTYPE[prec], "data": "synthetic (seeded droplet, NumPy PCG64)",
-               "config": config_dict(a.workload, p), "roofline": roof, "cpu_baseline": cpu,
+               "config": dict(config_dict(a.workload, ps), launch=launch), "roofline": roof, "cpu_baseline": cpu,
                "e2e": e2e, "clocks": clk.summary(), "gpu_launches": s.launches_per_step() * a.steps,
                "status": lbfe._lib.lbfe_status_str(st).decode(),
                "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
@@ -300,7 +325,8 @@ def run_reference(a):
     O.build()
     prec = {"fp32": 0, "fp16": 1, "bf16": 2}[a.precision]
     from paper_1411_2181_gb300 import configs
-    p, rho = workload(a.workload, prec)
+    ps, rhos = workload(a.workload, prec)
+    p, rho = ps[0], rhos[0]
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     d = p.oracle_dict()
     # each timed step: one oracle step on a z-slab of the box, sized so the
@@ -321,7 +347,7 @@ def run_reference(a):
     out = {"impl": "reference", "metric": METRIC, "value": round(mlups, 4), "unit": METRIC, "n_gpus": a.gpus,
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(dt / a.steps * 1e3, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic (seeded droplet, NumPy PCG64)", "config": config_dict(a.workload, p),
+           "data": "synthetic (seeded droplet, NumPy PCG64)", "config": config_dict(a.workload, ps),
            "cpu_baseline": {"value": round(mlups, 4), "unit": METRIC, "cores": cores, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": round(mlups, 4), "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -134,7 +134,8 @@ size_t lbfe_params_size(void);
 size_t lbfe_obs_size(void);
 
 /* Validate p and fill the derived numbers.  BAD_PARAM on: a non-positive
- * lattice size, Lz < 2, a solvent viscosity <= 0 (eta_P too large), BGK
+ * lattice size, Lz < 2, Lx > 4096, more than 2^26 cells in one instance
+ * (larger boxes: split into a batch), a solvent viscosity <= 0 (eta_P too large), BGK
  * tau <= 1/2, tau_P <= 0, L^2 <= 3, Uw >= 0.1 (Mach limit), an unknown
  * phase or precision.  out may be NULL. */
 lbfe_status lbfe_derive(const lbfe_params *p, lbfe_derived *out);

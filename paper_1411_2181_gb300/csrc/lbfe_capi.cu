@@ -52,7 +52,8 @@ struct Derived {
 // bulk total density rho_in + rho_out.
 lbfe_status derive(const lbfe_params &p, Derived &d) {
     if (p.Lx < 1 || p.Ly < 1 || p.Lz < 2 || p.Lx > 4096) return LBFE_ERR_BAD_PARAM;
-    if ((long long)p.Lx * p.Ly * p.Lz > (1LL << 40)) return LBFE_ERR_BAD_PARAM;
+    // the step kernel addresses fields with 32-bit offsets: (s*19 + i)*S + n < 2^32
+    if ((long long)p.Lx * p.Ly * p.Lz > (1LL << 26)) return LBFE_ERR_BAD_PARAM;
     if (p.precision < LBFE_FP32 || p.precision > LBFE_BF16_OFFSET) return LBFE_ERR_BAD_PARAM;
     if (p.visco_phase < 0 || p.visco_phase > 2) return LBFE_ERR_BAD_PARAM;
     if (!(p.tau_P > 0.0) || !(p.L2 > 3.0) || !(p.rho_in > 0.0) || !(p.rho_out >= 0.0)) return LBFE_ERR_BAD_PARAM;

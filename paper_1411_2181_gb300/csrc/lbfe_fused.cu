@@ -35,7 +35,6 @@ struct Geom {
     static constexpr int NT = TX * TY;                 // threads = tile cells
     static constexpr int RX = TX + 4, RY = TY + 4;     // radius-2 region
     static constexpr int R2N = RX * RY;
-    static constexpr int NHALO = R2N - NT;             // radius-2 cells outside the tile
     static constexpr int NRING1 = 2 * (RX - 2) + 2 * TY;  // radius-1 cells outside the tile
     // rings: rho (float2) x3, stress scalars (a f, a) x3, j 3x2, C 6x4, u 3x3
     static constexpr int FLOATS = (2 * 3 + 2 * 3 + 6 + 24 + 9) * R2N;
@@ -56,23 +55,6 @@ __device__ __forceinline__ float ldpop(const T *p, float add) {
     float v = Store<T>::ld(p);
     if (Store<T>::offset) v += add;
     return v;
-}
-
-// Halo cell h (0 <= h < NHALO) of the radius-2 region: two rows below and
-// above the tile (full width), then two columns left and right of it.
-template <int TY>
-__device__ __forceinline__ void halo2_coord(int h, int &gx, int &gy) {
-    using Gm = Geom<TY>;
-    if (h < 4 * Gm::RX) {
-        const int rr = h / Gm::RX;
-        gx = h - rr * Gm::RX;
-        gy = rr < 2 ? rr : Gm::RY - 4 + rr;
-    } else {
-        const int h2 = h - 4 * Gm::RX;
-        const int cc = h2 / TY;
-        gy = 2 + (h2 - cc * TY);
-        gx = cc < 2 ? cc : Gm::RX - 4 + cc;
-    }
 }
 
 // Ring cell h (0 <= h < NRING1) of the radius-1 region.

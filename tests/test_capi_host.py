@@ -47,7 +47,8 @@ def test_parameter_validation_on_host(lbfe):
     assert abs(d["De"] - 1.0) < 1e-12
     assert d["tau_A"] > 0.5 and d["tau_B"] > 0.5
     bad = [dict(Lz=1), dict(tau_P=0.0), dict(L2=3.0), dict(Uw=0.2), dict(eta_P=10.0),
-           dict(visco_phase=5), dict(precision=9), dict(eta_M=-1.0), dict(Lx=0)]
+           dict(visco_phase=5), dict(precision=9), dict(eta_M=-1.0), dict(Lx=0),
+           dict(Lx=4097), dict(Lx=4096, Ly=4096, Lz=5)]
     from dataclasses import replace
     for kw in bad:
         with pytest.raises(lbfe.LbfeError) as ei:
