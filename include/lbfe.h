@@ -181,6 +181,35 @@ lbfe_status lbfe_tune(lbfe_handle *h, int tile_y, int z_chunk);
  * instance 0, persistent grid size and number of work items. */
 lbfe_status lbfe_launch_config(const lbfe_handle *h, int *tile_y, int *z_chunk, int *grid, int *items);
 
+/* Observables of a population field the caller already holds on the
+ * device, computed without allocating anything.  For callers that cannot
+ * allocate device memory at the point where they want diagnostics: their
+ * memory belongs to another allocator whose pool must not be bypassed, they
+ * run under a device-memory budget fixed at start-up, or they cannot afford
+ * the device-wide synchronisation of cudaFree in a latency-sensitive loop.
+ * The paper has no counterpart of this entry point.
+ *   p       parameters of the field (sizes, precision, storage offsets rho0;
+ *           validated as in lbfe_derive);
+ *   f_dev   device pointer to populations [2][19][stride] in the storage
+ *           type of p->precision, in the layout and order of this header;
+ *   stride  elements between population arrays, >= Lx*Ly*Lz;
+ *   out     host result (same fields and readings as lbfe_observables;
+ *           step and t_over_tem are 0);
+ *   stream  cudaStream_t or NULL; synchronised before return.
+ * Scratch lives in a file-scope device array of about 200 KB that every
+ * GPU loading the library keeps until the process exits, so Lx is limited
+ * to 4096: larger Lx returns LBFE_ERR_BAD_PARAM before any device work.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  Every call shares the array and it keeps the last
+ * call's contents (each call clears what must start at zero).  Host calls
+ * are serialised and each synchronises its stream, so calls made through
+ * this function do not overlap; calls that did overlap on the GPU would race
+ * on the shared array.  Calls no cudaMalloc, cudaFree or other allocating
+ * routine. */
+lbfe_status lbfe_observables_noalloc(const lbfe_params *p, const void *f_dev, long long stride, lbfe_obs *out,
+                                     void *stream);
+
 /* Release the handle (the device block stays the caller's). */
 lbfe_status lbfe_destroy(lbfe_handle *h);
 

@@ -73,6 +73,8 @@ _lib.lbfe_tune.argtypes = [_H, ct.c_int, ct.c_int]
 _lib.lbfe_tune.restype = ct.c_int
 _lib.lbfe_launch_config.argtypes = [_H] + [ct.POINTER(ct.c_int)] * 4
 _lib.lbfe_launch_config.restype = ct.c_int
+_lib.lbfe_observables_noalloc.argtypes = [_P, ct.c_void_p, ct.c_longlong, ct.POINTER(CObs), ct.c_void_p]
+_lib.lbfe_observables_noalloc.restype = ct.c_int
 for _fn in ("lbfe_derive", "lbfe_required_bytes", "lbfe_create", "lbfe_init", "lbfe_step",
             "lbfe_observables", "lbfe_check", "lbfe_get_field", "lbfe_set_field", "lbfe_destroy"):
     getattr(_lib, _fn).restype = ct.c_int
@@ -125,6 +127,16 @@ def obs_to_dict(o: CObs) -> dict:
                 M=tuple(o.M), D=o.D, theta_deg=o.theta_deg, Lp=o.Lp, Lp_over_2R=o.Lp_over_2R,
                 t_over_tem=o.t_over_tem, necks=o.necks, fragments=o.fragments, broken=o.broken,
                 flags=o.flags)
+
+
+def observables_noalloc(p: Params, f_dev_ptr: int, stride: int, stream_ptr: int = 0) -> dict:
+    """Observables of a device population field the caller holds (see
+    ``lbfe_observables_noalloc``): no allocation inside the call."""
+    o = CObs()
+    c = _to_c(p)
+    _check(_lib.lbfe_observables_noalloc(ct.byref(c), ct.c_void_p(f_dev_ptr), int(stride), ct.byref(o),
+                                         ct.c_void_p(stream_ptr)), "lbfe_observables_noalloc")
+    return obs_to_dict(o)
 
 
 class Solver:
