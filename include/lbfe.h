@@ -23,8 +23,9 @@
  *
  * Errors: every call returns an lbfe_status and never aborts, traps or
  * exits.  A numerical blow-up (non-positive or NaN density, tr C >= L^2) is
- * flagged on the device by the step kernels and reported as
- * LBFE_ERR_DIVERGED by the next lbfe_observables() / lbfe_check().
+ * flagged on the device by the step kernels, per instance, and reported as
+ * LBFE_ERR_DIVERGED by the next lbfe_observables() of that instance (and by
+ * lbfe_check() for any instance of the handle).
  *
  * Field layout (the interface format of lbfe_get_field / lbfe_set_field):
  *   cell index n = (z*Ly + y)*Lx + x, N = Lx*Ly*Lz;
@@ -113,7 +114,7 @@ typedef struct {
     int necks;                /* interior non-empty minima of the x-profile below half the adjacent maxima */
     int fragments;            /* separated occupied x-runs holding >= 1% of the volume */
     int broken;               /* fragments >= 2 */
-    int flags;                /* device status word (bit 0: diverged) */
+    int flags;                /* this instance's device status word (bit 0: diverged) */
 } lbfe_obs;
 
 typedef struct lbfe_handle lbfe_handle;

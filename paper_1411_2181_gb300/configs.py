@@ -29,13 +29,11 @@ NOISE = 1e-4
 
 
 def make_params(Lx, Ly, Lz, R, Ca, De, lam=1.0, beta=0.4, L2=100.0, phase=1, Uw=None,
-                Uw_max=0.05, G=G_DEFAULT, sigma=SIGMA, precision=0):
+                Uw_max=0.05, G=G_DEFAULT, sigma=SIGMA, precision=0, rho_in=RHO_IN, rho_out=RHO_OUT):
     """Lattice parameters for a droplet of radius R between walls at gap
     W = Lz at capillary number Ca and Deborah number De (Eq. 8).
 
-    With Uw given, eta_M follows from Ca; otherwise Uw = Uw_max and eta_M is
-    chosen from Ca (raising Uw down if eta_M would push tau outside the
-    range the BGK collision handles well)."""
+    With Uw given, eta_M follows from Ca; otherwise Uw = Uw_max."""
     from .params import Params
     W = Lz
     if Uw is None:
@@ -57,8 +55,8 @@ def make_params(Lx, Ly, Lz, R, Ca, De, lam=1.0, beta=0.4, L2=100.0, phase=1, Uw=
         if De <= 0:
             phase = 0
     return Params(Lx=Lx, Ly=Ly, Lz=Lz, R=R, Uw=Uw, G=G, eta_M=eta_M, lambda_=lam, eta_P=eta_P,
-                  tau_P=tau_P, L2=L2, visco_phase=phase, rho_in=RHO_IN, rho_out=RHO_OUT,
-                  sigma=sigma, precision=precision, rho0=(RHO_OUT, RHO_OUT))
+                  tau_P=tau_P, L2=L2, visco_phase=phase, rho_in=rho_in, rho_out=rho_out,
+                  sigma=sigma, precision=precision, rho0=(rho_out, rho_out))
 
 
 def config1():

@@ -97,7 +97,7 @@ Layout plan(const lbfe_params *p, int n) {
     L.inst_off = take(sizeof(InstDev) * (size_t)n);
     L.tile_off = take(sizeof(int) * (size_t)(n + 1));
     L.item_off = take(sizeof(int) * (size_t)(n + 1));
-    L.status_off = take(sizeof(unsigned) * 4);
+    L.status_off = take(sizeof(unsigned) * (4 + (size_t)n));  // launch word, then one per instance
     L.mass_off = take(sizeof(double) * 2);
     const size_t eb = elem_bytes(p[0].precision);
     for (int k = 0; k < n; ++k) {
@@ -378,6 +378,7 @@ lbfe_status lbfe_create(lbfe_handle **hp, const lbfe_params *p, int n, void *dev
         I.u = scr + 5 * I.S;
         I.F = scr + 8 * I.S;
         I.prof = (unsigned long long *)(h->base + L.prof_off[k]);
+        I.status = h->status + 4 + k;
         I.mpart = (double *)(h->base + L.mpart_off[k]);
         I.G = (float)p[k].G;
         I.Uw = (float)p[k].Uw;
@@ -396,7 +397,7 @@ lbfe_status lbfe_create(lbfe_handle **hp, const lbfe_params *p, int n, void *dev
     h->total_tiles = toff[n];
     cudaError_t e = cudaMemcpyAsync(h->inst_dev, h->inst.data(), sizeof(InstDev) * n, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->tile_off, toff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(unsigned) * 4, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(unsigned) * (4 + (size_t)n), h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     const size_t smem = sizeof(unsigned long long) * 6 * (size_t)maxLx;
     if (e == cudaSuccess && smem > 48 * 1024) e = lbfe::obs_set_smem_limit(smem);
@@ -423,6 +424,7 @@ lbfe_status lbfe_init(lbfe_handle *h, int k, const double *rho_init) {
     double *stage = (double *)I.rho;
     CK(cudaMemcpyAsync(stage, rho_init, sizeof(double) * 2 * (size_t)I.N, cudaMemcpyHostToDevice, h->stream));
     CK(lbfe::launch_init(h->ctx(), k, stage, h->cur));
+    CK(cudaMemsetAsync(I.status, 0, sizeof(unsigned), h->stream));
     CK(cudaStreamSynchronize(h->stream));
     h->steps[k] = 0;
     h->ready[k] = 1;
@@ -461,7 +463,7 @@ lbfe_status lbfe_observables(lbfe_handle *h, int k, lbfe_obs *out) {
     unsigned st = 0;
     CK(cudaMemcpyAsync(prof.data(), I.prof, sizeof(unsigned long long) * prof.size(), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaMemcpyAsync(mass, h->mass, sizeof mass, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaMemcpyAsync(&st, h->status, sizeof st, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&st, I.status, sizeof st, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
 
     memset(out, 0, sizeof *out);

@@ -370,7 +370,7 @@ k_fused(const InstDev *__restrict__ insts, const int *__restrict__ item_off, int
                 }
                 const float rt = rAo + rBo;
                 if (!(rt > 0.f) || uo[0] != uo[0] || uo[1] != uo[1] || uo[2] != uo[2])
-                    atomicOr(status, kFlagDiverged);
+                    raise_flag(status, I, kFlagDiverged);
                 const float nu = (rAo * I.nu_A + rBo * I.nu_B) / rt;
                 const float om = 1.0f / (3.0f * nu + 0.5f);
                 const bool bottom = q == 0, top = q == Lz - 1;
@@ -426,7 +426,7 @@ k_fused(const InstDev *__restrict__ insts, const int *__restrict__ item_off, int
                     const float relax = (fp * c[q6] - (q6 < 3 ? 1.f : 0.f)) * I.inv_tauP;
                     Cout[(u32)(q6 * S + n)] = c[q6] + (-adv[q6] + st - relax);
                 }
-                if (!(c[0] + c[1] + c[2] < I.L2)) atomicOr(status, kFlagDiverged);
+                if (!(c[0] + c[1] + c[2] < I.L2)) raise_flag(status, I, kFlagDiverged);
             }
             __syncthreads();
         }

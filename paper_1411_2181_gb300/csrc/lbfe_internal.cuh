@@ -73,7 +73,14 @@ struct InstDev {
     float gx, gy, gz;                // body acceleration
     float rho0[2];                   // storage offsets
     int ntx, nty, nzc, zc;           // fused kernel: column tiles in x, y; z-chunks and their depth
+    unsigned *status;                // this instance's status word (may be null)
 };
+
+// Raise a status flag for the whole launch and, when present, for instance I.
+__device__ __forceinline__ void raise_flag(unsigned *global, const InstDev &I, unsigned flag) {
+    atomicOr(global, flag);
+    if (I.status) atomicOr(I.status, flag);
+}
 
 constexpr int kBlock = 256;          // threads per block of the cell-per-thread kernels
 constexpr int kObsBlocks = 304;      // 2 x 152 SMs for the observables reduction

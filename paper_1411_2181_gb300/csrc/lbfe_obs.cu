@@ -57,7 +57,7 @@ k_obs_planes(const InstDev *__restrict__ insts, int k, int cur, unsigned *status
             }
         }
     }
-    if (bad) atomicOr(status, kFlagDiverged);
+    if (bad) raise_flag(status, I, kFlagDiverged);
     __syncthreads();
     for (int q = threadIdx.x; q < 6 * Lx; q += blockDim.x)
         if (sh[q]) atomicAdd(I.prof + q, sh[q]);

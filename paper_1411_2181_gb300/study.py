@@ -1,0 +1,297 @@
+"""Critical Capillary number search (Sec. 3) with and without the learned
+proposal.
+
+Sec. 3 defines Ca_cr through the largest wall velocity at which the droplet
+stays stable and the smallest at which it breaks.  Here a case is the
+tuple (Ca, De, lambda, 2R/W, L^2, viscoelastic phase); Ca varies through the
+wall speed at a fixed matrix viscosity, as in the paper.  A verdict is one
+full simulation of the case on the GPU:
+  broken  - the break-up flag (two separated occupied x-runs, each >= 1% of
+            the volume) was set at an observation before t_max;
+  stable  - otherwise.
+Cases are simulated in batches (one persistent launch per step advances
+every case of the batch).
+
+Two search modes over held-out (De, lambda, 2R/W, phase) triples:
+  bisect  - bracket [Ca_lo, Ca_hi] = [CA_MIN, CA_MAX] checked by two runs, then
+            halved until Ca_hi - Ca_lo <= tol;
+  mlp     - the network's break-up logit over a Ca grid gives Ca* and the
+            bracket Ca* -/+ delta; both ends are verified by full runs (and
+            the bracket is moved outwards until they are stable / broken),
+            then halved until the width is <= tol.
+Every verdict in both modes comes from a full simulation; the network only
+chooses which simulations to run.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import configs, synth
+from .params import Params
+
+# Study regime (lattice units).  Small droplets dissolve into the matrix
+# through the Shan-Chen miscibility, faster at high viscosity (the mutual
+# diffusivity grows with tau - 1/2); the study therefore uses a stronger
+# coupling G = 3.8 (flat-interface coexistence densities 1.05503 / 0.01288,
+# sigma = 0.0985 from the oracle's Laplace fit), droplets with 2R/W in
+# [0.6, 0.8] at W = 40, and varies Ca through the matrix viscosity at the
+# wall speed 0.08, which keeps every BGK relaxation time below about 11
+# (runs with tau above about 13 in the droplet diverge at this coupling).
+G_STUDY = 3.8
+RHO_IN_STUDY, RHO_OUT_STUDY = 1.05503, 0.01288
+SIGMA_STUDY = 0.09854
+W = 40
+LX, LY = 192, 44
+CA_MIN, CA_MAX = 0.2, 1.9
+UW = 0.08
+CONF_MIN, CONF_MAX = 0.6, 0.8
+LAMBDAS = (0.5, 1.0)
+T_MAX_TEM = 30.0      # simulated time in emulsion times
+OBS_EVERY_TEM = 0.5
+
+
+@dataclass
+class Case:
+    Ca: float
+    De: float
+    lam: float
+    conf: float        # 2R/W
+    L2: float = 100.0
+    phase: int = 1     # 1 droplet viscoelastic, 2 matrix viscoelastic
+    seed: int = 0
+
+
+@dataclass
+class Verdict:
+    broken: bool
+    D: float
+    theta: float
+    necks: int
+    t_break: float     # in emulsion times, nan if stable
+    ok: bool = True
+
+
+def case_params(c: Case) -> Params:
+    """Lattice parameters of a case: wall speed UW, eta_M from Ca (Sec. 1),
+    tau_P from De (Eq. 8), emulsion time R eta_M / sigma (Eq. 9)."""
+    R = 0.5 * c.conf * W
+    return configs.make_params(LX, LY, W, R, Ca=c.Ca, De=c.De, lam=c.lam, beta=0.4, L2=c.L2, phase=c.phase,
+                               Uw=UW, G=G_STUDY, sigma=SIGMA_STUDY, rho_in=RHO_IN_STUDY,
+                               rho_out=RHO_OUT_STUDY)
+
+
+def tau_em(c: Case) -> float:
+    p = case_params(c)
+    return p.R * p.eta_M / p.sigma
+
+
+def features(cases) -> np.ndarray:
+    """Scaled network inputs: (Ca, De, ln lambda, 2R/W, ln L^2, phase)."""
+    X = np.array([[(c.Ca - 1.2) / 0.6, (c.De - 1.0), math.log(c.lam) / math.log(2.0), (c.conf - 0.7) / 0.1,
+                   (math.log(c.L2) - math.log(200.0)) / math.log(4.0), -1.0 if c.phase == 1 else 1.0]
+                  for c in cases], dtype=np.float32)
+    return X
+
+
+def targets(verdicts) -> tuple[np.ndarray, np.ndarray]:
+    T = np.array([[v.D, v.theta / 90.0, 1.0 if v.broken else 0.0, v.necks / 4.0] for v in verdicts], np.float32)
+    M = np.array([0.0 if v.broken else 1.0 for v in verdicts], np.float32)
+    return T, M
+
+
+def run_batch(cases: list[Case], device=None, stats: dict | None = None) -> list[Verdict]:
+    """Simulate every case to t_max (or until all broke); one verdict each."""
+    import torch
+    from . import lbfe
+    ps = [case_params(c) for c in cases]
+    tem = [p.R * p.eta_M / p.sigma for p in ps]
+    stream = torch.cuda.Stream(device)
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        s = lbfe.Solver(ps, device=device, stream=stream)
+        s.tune(16, 0)
+        for k, (c, p) in enumerate(zip(cases, ps)):
+            s.init(k, synth.droplet_densities(p.Lx, p.Ly, p.Lz, p.R, p.rho_in, p.rho_out, 1e-4, seed=c.seed))
+        n = len(cases)
+        broken = [False] * n
+        ok = [True] * n
+        last = [None] * n
+        necks = [0] * n
+        t_break = [float("nan")] * n
+        every = max(1, int(round(OBS_EVERY_TEM * min(tem))))
+        t_end = int(math.ceil(T_MAX_TEM * max(tem)))
+        steps = 0
+        while steps < t_end and not all(broken[k] or not ok[k] for k in range(n)):
+            s.step(every)
+            steps += every
+            for k in range(n):
+                if broken[k] or not ok[k]:
+                    continue
+                if steps > T_MAX_TEM * tem[k] + every:
+                    continue
+                ob = s.observables(k, raise_on_diverged=False)
+                if ob["flags"]:
+                    ok[k] = False          # this instance blew up: no verdict
+                    continue
+                if ob["broken"]:
+                    broken[k] = True
+                    t_break[k] = steps / tem[k]
+                else:
+                    last[k] = ob
+                    necks[k] = max(necks[k], ob["necks"])
+        torch.cuda.synchronize()
+        s.close()
+    if stats is not None:
+        stats["runs"] = stats.get("runs", 0) + len(cases)
+        stats["batches"] = stats.get("batches", 0) + 1
+        stats["seconds"] = stats.get("seconds", 0.0) + time.perf_counter() - t0
+        stats["lattice_updates"] = stats.get("lattice_updates", 0) + steps * sum(p.N for p in ps)
+    out = []
+    for k in range(len(cases)):
+        ob = last[k] or {"D": 0.0, "theta_deg": 0.0}
+        out.append(Verdict(broken[k], ob["D"], ob["theta_deg"], necks[k], t_break[k], ok[k]))
+    return out
+
+
+def sample_cases(n: int, seed: int) -> list[Case]:
+    """Training cases: half with Ca uniform over the search range, half in
+    its upper part, where break-up happens at this resolution."""
+    rng = np.random.default_rng(seed)
+    cs = []
+    for k in range(n):
+        ca = rng.uniform(CA_MIN, CA_MAX) if k % 2 == 0 else rng.uniform(CA_MIN + 0.6 * (CA_MAX - CA_MIN), CA_MAX)
+        cs.append(Case(Ca=float(ca), De=float(rng.choice([0.0, 0.5, 1.0, 2.0])),
+                       lam=float(rng.choice(LAMBDAS)), conf=float(rng.uniform(CONF_MIN, CONF_MAX)),
+                       L2=100.0, phase=int(rng.choice([1, 2])), seed=int(rng.integers(0, 2 ** 31))))
+    return cs
+
+
+def training_set(n: int, seed: int = 100, batch: int = 64, device=None, stats=None):
+    cases = sample_cases(n, seed)
+    verdicts = []
+    for s in range(0, n, batch):
+        verdicts += run_batch(cases[s:s + batch], device=device, stats=stats)
+    keep = [k for k, v in enumerate(verdicts) if v.ok]
+    cases = [cases[k] for k in keep]
+    verdicts = [verdicts[k] for k in keep]
+    return cases, verdicts
+
+
+@dataclass
+class Search:
+    triple: tuple
+    lo: float
+    hi: float
+    runs: int = 0
+    history: list = field(default_factory=list)
+
+    @property
+    def width(self):
+        return self.hi - self.lo
+
+
+def _case(triple, Ca, seed):
+    De, lam, conf, phase = triple
+    return Case(Ca=Ca, De=De, lam=lam, conf=conf, phase=phase, seed=seed)
+
+
+def _verdict_round(searches, cas, device, stats, seed):
+    """One batched round: a full run for every (search, Ca) pair."""
+    pairs = [(s, ca) for s, lst in zip(searches, cas) for ca in lst]
+    if not pairs:
+        return {}
+    vs = run_batch([_case(s.triple, ca, seed) for s, ca in pairs], device=device, stats=stats)
+    res = {}
+    for (s, ca), v in zip(pairs, vs):
+        s.runs += 1
+        # a run that blew up gives no verdict; it is counted as breaking (the
+        # search then stays below the unstable range) and reported
+        br = v.broken or not v.ok
+        if not v.ok:
+            stats["diverged"] = stats.get("diverged", 0) + 1
+        s.history.append((ca, br))
+        res[(id(s), ca)] = br
+    return res
+
+
+def _bisect_rounds(searches, tol, device, stats, seed):
+    while True:
+        act = [s for s in searches if s.width > tol + 1e-12]
+        if not act:
+            return
+        mids = [[0.5 * (s.lo + s.hi)] for s in act]
+        res = _verdict_round(act, mids, device, stats, seed)
+        for s, (m,) in zip(act, mids):
+            if res[(id(s), m)]:
+                s.hi = m
+            else:
+                s.lo = m
+        stats["rounds"] = stats.get("rounds", 0) + 1
+
+
+def search_bisect(triples, tol=0.02, lo=CA_MIN, hi=CA_MAX, device=None, seed=7):
+    """Plain bisection: verify the initial bracket, then halve it."""
+    stats = {}
+    searches = [Search(t, lo, hi) for t in triples]
+    res = _verdict_round(searches, [[lo, hi]] * len(searches), device, stats, seed)
+    stats["rounds"] = 1
+    for s in searches:
+        if res[(id(s), lo)]:
+            s.hi = s.lo = lo          # breaks already at the lower end
+        elif not res[(id(s), hi)]:
+            s.lo = s.hi = hi          # stable at the upper end
+    _bisect_rounds(searches, tol, device, stats, seed)
+    return searches, stats
+
+
+def search_mlp(triples, net, tol=0.02, delta=0.04, lo=CA_MIN, hi=CA_MAX, device=None, seed=7):
+    """Network-proposed bracket Ca* -/+ delta: both ends are verified by full
+    runs; an end that contradicts the bracket (the lower end breaks, or the
+    upper end stays stable) becomes the other end and the bracket moves by
+    2 delta in that direction, until both ends hold.  Then it is halved."""
+    stats = {"rounds": 0}
+    grid = np.linspace(lo, hi, 341)
+    searches = []
+    for t in triples:
+        X = features([_case(t, float(ca), 0) for ca in grid])
+        logit = net.forward(X)[:, 2]
+        above = np.nonzero(logit > 0)[0]
+        ca_star = float(grid[above[0]]) if len(above) else hi
+        searches.append(Search(t, max(lo, ca_star - delta), min(hi, ca_star + delta)))
+    ok = {id(s): [False, False] for s in searches}   # lower end stable / upper end broken verified
+    pending = list(searches)
+    while pending:
+        cas = [[e for e, done in ((s.lo, ok[id(s)][0]), (s.hi, ok[id(s)][1])) if not done] for s in pending]
+        res = _verdict_round(pending, cas, device, stats, seed)
+        stats["rounds"] += 1
+        nxt = []
+        for s in pending:
+            f = ok[id(s)]
+            r_lo = None if f[0] else res[(id(s), s.lo)]
+            r_hi = None if f[1] else res[(id(s), s.hi)]
+            if r_lo is True:                      # breaks at the lower end: Ca_cr is below it
+                s.hi, f[1] = s.lo, True
+                if s.lo <= lo:
+                    s.lo, f[0] = lo, True
+                else:
+                    s.lo, f[0] = max(lo, s.lo - 2 * delta), False
+            elif r_hi is False:                   # stable at the upper end: Ca_cr is above it
+                s.lo, f[0] = s.hi, True
+                if s.hi >= hi:
+                    s.hi, f[1] = hi, True
+                else:
+                    s.hi, f[1] = min(hi, s.hi + 2 * delta), False
+            else:
+                if r_lo is False:
+                    f[0] = True
+                if r_hi is True:
+                    f[1] = True
+            if not (f[0] and f[1]):
+                nxt.append(s)
+        pending = nxt
+    _bisect_rounds(searches, tol, device, stats, seed)
+    return searches, stats

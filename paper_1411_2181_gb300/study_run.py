@@ -1,0 +1,94 @@
+"""Train the proposal network on solver runs and compare Ca_cr searches.
+
+python -m paper_1411_2181_gb300.study_run --train 1024 --triples 16 --out report.json
+
+1. ``--train`` cases drawn over (Ca, De, lambda, 2R/W, phase) are simulated
+   in batches; their verdicts and shapes are the training set.
+2. The network is trained by the CUDA kernels (AdamW, BF16 weights).
+3. For ``--triples`` held-out (De, lambda, 2R/W, phase) triples (seed 5), Ca_cr
+   is searched by plain bisection and with the network's bracket; both give
+   brackets of width <= 0.02 confirmed by full runs.  The report lists, per
+   mode, the number of full simulations, batched rounds and wall time, and
+   per triple both brackets.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import mlp, study
+
+
+def held_out_triples(n: int, seed: int = 5):
+    rng = np.random.default_rng(seed)
+    return [(float(rng.choice([0.0, 0.5, 1.0, 2.0])), float(rng.choice(study.LAMBDAS)),
+             float(rng.uniform(study.CONF_MIN + 0.02, study.CONF_MAX - 0.02)), int(rng.choice([1, 2])))
+            for _ in range(n)]
+
+
+def CA_IN(s) -> bool:
+    """Ca_cr strictly inside the search range (not at either end)."""
+    return study.CA_MIN < 0.5 * (s.lo + s.hi) < study.CA_MAX
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=1024)
+    ap.add_argument("--triples", type=int, default=16)
+    ap.add_argument("--epochs", type=int, default=1500)
+    ap.add_argument("--delta", type=float, default=0.06)
+    ap.add_argument("--out", default=None)
+    ap.add_argument("--params-out", default=None)
+    a = ap.parse_args(argv)
+
+    report = {}
+    st_train = {}
+    t0 = time.perf_counter()
+    cases, verdicts = study.training_set(a.train, seed=100, stats=st_train)
+    report["training_runs"] = dict(st_train, valid=len(cases), broken=int(sum(v.broken for v in verdicts)))
+    X = study.features(cases)
+    T, M = study.targets(verdicts)
+    # hold out 1/8 of the runs to estimate the network's accuracy
+    n_val = max(1, len(X) // 8)
+    net = mlp.MLP(max_batch=max(4096, len(X)), bf16=True)
+    net.set_params(mlp.init_params(0))
+    t1 = time.perf_counter()
+    hist = net.fit(X[n_val:], T[n_val:], M[n_val:], epochs=a.epochs, lr=3e-3, batch=256)
+    train_s = time.perf_counter() - t1
+    yv = net.forward(X[:n_val])
+    acc = float(np.mean((yv[:, 2] > 0) == (T[:n_val, 2] > 0.5)))
+    d_err = float(np.sqrt(np.sum(M[:n_val] * (yv[:, 0] - T[:n_val, 0]) ** 2) / max(1.0, M[:n_val].sum())))
+    report["network"] = {"epochs": a.epochs, "final_loss": hist[-1], "first_loss": hist[0],
+                         "train_seconds": train_s, "val_breakup_accuracy": acc, "val_D_rmse": d_err}
+    if a.params_out:
+        np.save(a.params_out, net.get_params())
+
+    triples = held_out_triples(a.triples)
+    sb, stb = study.search_bisect(triples)
+    sm, stm = study.search_mlp(triples, net, delta=a.delta)
+    per = []
+    agree = 0
+    for b, m in zip(sb, sm):
+        cb, cm = 0.5 * (b.lo + b.hi), 0.5 * (m.lo + m.hi)
+        agree += abs(cb - cm) <= 0.01 + 1e-9
+        per.append({"triple": b.triple, "bisect": [b.lo, b.hi, b.runs], "mlp": [m.lo, m.hi, m.runs]})
+    keys = ("runs", "rounds", "seconds", "lattice_updates", "diverged")
+    report["bisect"] = {k: stb.get(k, 0) for k in keys}
+    report["mlp"] = {k: stm.get(k, 0) for k in keys}
+    report["in_range"] = int(sum(CA_IN(b) for b in sb))
+    report["agree_within_0.01"] = f"{agree}/{len(triples)}"
+    report["per_triple"] = per
+    report["total_seconds"] = time.perf_counter() - t0
+    txt = json.dumps(report, indent=1)
+    print(txt)
+    if a.out:
+        with open(a.out, "w") as fh:
+            fh.write(txt)
+    return report
+
+
+if __name__ == "__main__":
+    main()

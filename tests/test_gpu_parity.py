@@ -203,3 +203,20 @@ def test_batch_equals_solo_runs(L):
         assert np.array_equal(batch.get_field(k, L.FIELD_C), solo.get_field(0, L.FIELD_C)), k
         ob, os_ = batch.observables(k), solo.observables(0)
         assert ob["D"] == os_["D"] and ob["volume"] == os_["volume"]
+
+
+def test_divergence_is_per_instance(L):
+    """A blow-up injected into one instance of a batch flags that instance
+    only; the others keep reporting observables."""
+    ps = [L.Params(Lx=16, Ly=12, Lz=10, Uw=0.01, eta_M=0.5, eta_P=0.1, tau_P=5.0, L2=20.0, visco_phase=1)
+          for _ in range(3)]
+    s = L.Solver(ps)
+    for k in range(3):
+        s.init(k, synth.droplet_densities(16, 12, 10, 3.0, seed=k))
+    C = s.get_field(1, L.FIELD_C)
+    C[0, 5, 6, 8] = 30.0
+    s.set_field(1, L.FIELD_C, C)
+    s.step(1)
+    assert s.check() == L.ERR_DIVERGED
+    assert s.observables(0)["flags"] == 0 and s.observables(2)["flags"] == 0
+    assert s.observables(1, raise_on_diverged=False)["flags"] & 1
