@@ -57,8 +57,9 @@ typedef enum {
 
 typedef enum {
     LBFE_FP32 = 0,            /* populations stored in FP32 */
-    LBFE_FP16_OFFSET = 1,     /* stored as FP16 offsets f - w_i rho0_s, FP32 compute */
-    LBFE_BF16_OFFSET = 2      /* stored as BF16 offsets f - w_i rho0_s, FP32 compute */
+    LBFE_FP16_OFFSET = 1,     /* stored as FP16 offsets f - w_i rho_s', FP32 compute */
+    LBFE_BF16_OFFSET = 2      /* stored as BF16 offsets f - w_i rho_s', FP32 compute; rho_s' is
+                                 the cell's own density of the previous step, kept in FP32 */
 } lbfe_precision;
 
 typedef enum {
@@ -85,7 +86,7 @@ typedef struct {
     double rho_out;           /* bulk density of the dissolved component */
     double sigma;             /* interfacial tension of G (bookkeeping of Ca, De, tau_em) */
     double g[3];              /* constant body acceleration (verification hook; 0 normally) */
-    double rho0[2];           /* storage offsets of the reduced-precision forms, per component */
+    double rho0[2];           /* constant offsets of the reduced forms in lbfe_observables_noalloc */
 } lbfe_params;
 
 /* Derived numbers (host arithmetic only). */

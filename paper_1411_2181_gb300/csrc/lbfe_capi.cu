@@ -81,7 +81,7 @@ lbfe_status derive(const lbfe_params &p, Derived &d) {
 
 struct Layout {
     size_t inst_off, tile_off, item_off, status_off, mass_off;
-    std::vector<size_t> f_off[2], C_off[2], scratch_off, prof_off, mpart_off;
+    std::vector<size_t> f_off[2], C_off[2], scratch_off, prof_off, mpart_off, dens_off;
     size_t total;
 };
 
@@ -109,6 +109,8 @@ Layout plan(const lbfe_params *p, int n) {
         L.scratch_off.push_back(take(sizeof(float) * 14 * S));
         L.prof_off.push_back(take(sizeof(unsigned long long) * 6 * (size_t)p[k].Lx));
         L.mpart_off.push_back(take(sizeof(double) * 2 * lbfe::kObsBlocks));
+        // reduced storage forms: per-cell offset densities, ping-pong
+        L.dens_off.push_back(p[0].precision == LBFE_FP32 ? 0 : take(sizeof(float) * 2 * 2 * S));
     }
     L.total = off;
     return L;
@@ -390,6 +392,10 @@ lbfe_status lbfe_create(lbfe_handle **hp, const lbfe_params *p, int n, void *dev
         I.gx = (float)p[k].g[0]; I.gy = (float)p[k].g[1]; I.gz = (float)p[k].g[2];
         I.rho0[0] = (float)p[k].rho0[0];
         I.rho0[1] = (float)p[k].rho0[1];
+        if (p[0].precision != LBFE_FP32) {
+            I.dens[0] = (float2 *)(h->base + L.dens_off[k]);
+            I.dens[1] = I.dens[0] + I.S;
+        }
         h->inst.push_back(I);
         toff[k + 1] = toff[k] + (int)((I.N + lbfe::kBlock - 1) / lbfe::kBlock);
         if (p[k].Lx > maxLx) maxLx = p[k].Lx;
@@ -582,6 +588,21 @@ lbfe_status lbfe_set_field(lbfe_handle *h, int k, int which, const void *host_sr
             if (bytes != sizeof(float) * 2 * lbfe::Q * N) return LBFE_ERR_BAD_PARAM;
             float *tmp = I.u;
             const lbfe::LaunchCtx c = h->ctx();
+            if (I.dens[0]) {
+                // the new state is stored relative to its own densities
+                std::vector<float2> d(N);
+                for (size_t n = 0; n < N; ++n) {
+                    float a = 0.f, b = 0.f;
+                    for (int i = 0; i < lbfe::Q; ++i) {
+                        a += src[(size_t)i * N + n];
+                        b += src[(size_t)(lbfe::Q + i) * N + n];
+                    }
+                    d[n] = make_float2(a, b);
+                }
+                CK(cudaMemcpyAsync(I.dens[h->cur ^ 1], d.data(), sizeof(float2) * N, cudaMemcpyHostToDevice,
+                                   h->stream));
+                CK(cudaStreamSynchronize(h->stream));
+            }
             for (int s = 0; s < 2; ++s)
                 for (int i = 0; i < lbfe::Q; ++i) {
                     CK(cudaMemcpyAsync(tmp, src + (size_t)(s * lbfe::Q + i) * N, sizeof(float) * N,

@@ -37,13 +37,14 @@ __global__ void __launch_bounds__(kBlock)
 k_moments(const InstDev *__restrict__ insts, const int *__restrict__ tile_off, int n_inst, int cur) {
     LBFE_CELL_PROLOGUE
     const T *f = (const T *)I.f[cur];
+    const float2 od = offset_dens<T>(I, cur, n);
     // momentum from opposite-pair differences f_i - f_opp(i): the pair
     // members are close, so each difference is exact in FP32 and the large
     // cancellation of the plain signed sum is avoided
     float r[2], jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-        const float r0 = I.rho0[s];
+        const float r0 = s == 0 ? od.x : od.y;
         float v[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) v[i] = decode(f, (long long)(s * Q + i) * S + n, i, r0);
@@ -143,19 +144,26 @@ k_forces(const InstDev *__restrict__ insts, const int *__restrict__ tile_off, in
 
 // ---------------------------------------------------------------- init / IO
 template <typename T>
-__global__ void k_init(InstDev I, const double *__restrict__ rho0, int cur) {
+__global__ void k_init(InstDev I, const double *__restrict__ rho_init, int cur) {
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= I.N) return;
     T *f = (T *)I.f[cur];
     const long long S = I.S;
+    float off[2] = {I.rho0[0], I.rho0[1]};
+    if (Store<T>::offset && I.dens[0]) {
+        // the state is stored relative to its own densities
+        off[0] = (float)rho_init[n];
+        off[1] = (float)rho_init[I.N + n];
+        I.dens[cur ^ 1][n] = make_float2(off[0], off[1]);
+    }
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-        const double r = rho0[(long long)s * I.N + n];
+        const double r = rho_init[(long long)s * I.N + n];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const double w = i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
             double v = w * r;
-            if (Store<T>::offset) v -= w * (double)I.rho0[s];
+            if (Store<T>::offset) v -= w * (double)off[s];
             Store<T>::st(f + (long long)(s * Q + i) * S + n, (float)v);
         }
     }
@@ -170,7 +178,8 @@ __global__ void k_decode_pop(InstDev I, int cur, int s, int i, float *dst) {
     if (n >= I.N) return;
     const T *f = (const T *)I.f[cur];
     float v = Store<T>::ld_plain(f + (long long)(s * Q + i) * I.S + n);
-    if (Store<T>::offset) v += wq(i) * I.rho0[s];
+    const float2 od = offset_dens<T>(I, cur, n);
+    if (Store<T>::offset) v += wq(i) * (s == 0 ? od.x : od.y);
     dst[n] = v;
 }
 
@@ -180,7 +189,8 @@ __global__ void k_encode_pop(InstDev I, int cur, int s, int i, const float *src)
     if (n >= I.N) return;
     T *f = (T *)I.f[cur];
     float v = src[n];
-    if (Store<T>::offset) v -= wq(i) * I.rho0[s];
+    const float2 od = offset_dens<T>(I, cur, n);
+    if (Store<T>::offset) v -= wq(i) * (s == 0 ? od.x : od.y);
     Store<T>::st(f + (long long)(s * Q + i) * I.S + n, v);
 }
 

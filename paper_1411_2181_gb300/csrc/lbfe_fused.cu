@@ -21,6 +21,9 @@
 //                 conformation ring.
 // The collision of plane p-1 needs the densities of plane p (Shan-Chen); the
 // C update of plane p-2 needs the velocity of plane p-1, hence the lags.
+// Three block barriers per plane: after stage M, after stage X (stage X
+// needs only its own cell's forces, so it runs before the barrier that
+// stage U needs) and after stage U.
 // Planes beyond a wall are loaded as the adjacent plane (mirror ghosts of
 // rho, C and Pi); the velocity ghost 2 U_wall - u is applied in stage U.
 #include "lbfe_internal.cuh"
@@ -40,9 +43,10 @@ struct Geom {
     static constexpr int FLOATS = (2 * 3 + 2 * 3 + 6 + 24 + 9) * R2N;
 };
 
+// Ring slot of plane p (p >= -4) in rings of 2, 3 and 4 planes.
+__device__ __forceinline__ int ring2(int p) { return (p + 12) & 1; }
 __device__ __forceinline__ int ring3(int p) { return (p + 12) % 3; }
 __device__ __forceinline__ int ring4(int p) { return (p + 12) & 3; }
-__device__ __forceinline__ int ring2(int p) { return (p + 12) & 1; }
 __device__ __forceinline__ int wrapg(int a, int L) { a %= L; return a < 0 ? a + L : a; }
 
 // symmetric-tensor slot of (a, b): xx, yy, zz, xy, xz, yz
@@ -100,8 +104,9 @@ struct MCell {
 // field offset (s*19 + i)*S + n stays below 2^32.
 template <typename T>
 __device__ __forceinline__ void m_load(const InstDev &I, const T *__restrict__ fin, const float *__restrict__ Cin,
-                                       u32 S, u32 n, MCell &m) {
-    const float ra0 = I.rho0[0], rb0 = I.rho0[1];
+                                       u32 S, u32 n, int cur, MCell &m) {
+    const float2 od = offset_dens<T>(I, cur, n);
+    const float ra0 = od.x, rb0 = od.y;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         m.f[i] = ldpop(fin + (u32)(i * S + n), wq(i) * ra0);
@@ -115,6 +120,7 @@ __device__ __forceinline__ void m_load(const InstDev &I, const T *__restrict__ f
 // ring slots of its plane.
 template <int TY>
 __device__ __forceinline__ void m_store(const InstDev &I, const MCell &m, int idx, int s3, int s2, int s4) {
+    // s3: rho / stress slot, s2: j slot, s4: C slot of the plane
     constexpr int R2N = Geom<TY>::R2N;
     using Rg = Ring<TY>;
     float2 *rho_s = reinterpret_cast<float2 *>(smem() + Rg::RHO) + s3 * R2N;
@@ -150,9 +156,11 @@ __device__ __forceinline__ void m_store(const InstDev &I, const MCell &m, int id
 
 // Ring slots of the planes one iteration touches (q = p - 1, r = p - 2).
 struct Slots {
-    int r3[3];   // rho / pi / u slots of planes q-1, q, q+1 (plane r-1 = q-2 shares q+1's slot)
-    int c4[4];   // C slots of planes q-2, q-1, q, q+1
-    int j2;      // j slot of plane q
+    int r3[3];   // rho / stress / u slots of planes q-1, q, q+1
+    int ur[3];   // u slots of planes r-1, r, r+1 (= q-2, q-1, q)
+    int cf[3];   // C slots of planes q-1, q, q+1 (stage F)
+    int cu[3];   // C slots of planes r-1, r, r+1 (stage U)
+    int j3;      // j slot of plane q (ring of 2)
 };
 
 // Stage F for one cell of plane q: Shan-Chen and polymer forces and the
@@ -187,9 +195,9 @@ __device__ __forceinline__ void stage_f_cell(const InstDev &I, int idx, const Sl
         const float *sm_ = smem() + Rg::PI + L.r3[0] * 2 * R2N;
         const float *sc_ = smem() + Rg::PI + L.r3[1] * 2 * R2N;
         const float *sp_ = smem() + Rg::PI + L.r3[2] * 2 * R2N;
-        const float *cm = smem() + Rg::C + L.c4[1] * 6 * R2N;
-        const float *cc = smem() + Rg::C + L.c4[2] * 6 * R2N;
-        const float *cp = smem() + Rg::C + L.c4[3] * 6 * R2N;
+        const float *cm = smem() + Rg::C + L.cf[0] * 6 * R2N;
+        const float *cc = smem() + Rg::C + L.cf[1] * 6 * R2N;
+        const float *cp = smem() + Rg::C + L.cf[2] * 6 * R2N;
         const float afxp = sc_[idx + 1], afxm = sc_[idx - 1], afyp = sc_[idx + RX], afym = sc_[idx - RX];
         const float afzp = sp_[idx], afzm = sm_[idx];
 #pragma unroll
@@ -209,26 +217,49 @@ __device__ __forceinline__ void stage_f_cell(const InstDev &I, int idx, const Sl
     for (int a = 0; a < 3; ++a) {
         FA[a] = -I.G * rA * sA[a] + (rA * inv) * FP[a] + rA * g[a];
         FB[a] = -I.G * rB * sB[a] + (rB * inv) * FP[a] + rB * g[a];
-        u[a] = (smem()[Rg::J + L.j2 * 3 * R2N + a * R2N + idx] + 0.5f * (FA[a] + FB[a])) * inv;
+        u[a] = (smem()[Rg::J + L.j3 * 3 * R2N + a * R2N + idx] + 0.5f * (FA[a] + FB[a])) * inv;
         smem()[Rg::U + L.r3[1] * 3 * R2N + a * R2N + idx] = u[a];
     }
+}
+
+// Offsets of the reduced storage forms at the destination of a push:
+// the destination cell's densities of this step (from the density ring of
+// planes q-1, q, q+1), or the constant offsets when densities are not
+// tracked.
+struct PushOffsets {
+    const float2 *ring[3];   // density ring slots of planes q-1, q, q+1
+    int idx;                 // ring index of the pushing cell
+    float own[2];            // the pushing cell's densities
+    bool track;
+    float r0[2];             // constant offsets
+};
+
+template <int RX>
+__device__ __forceinline__ float push_offset(const PushOffsets &P, int s, int d, bool wall) {
+    if (!P.track) return P.r0[s];
+    if (wall) return P.own[s];
+    const float2 v = P.ring[cz(d) + 1][P.idx + cx(d) + cy(d) * RX];
+    return s == 0 ? v.x : v.y;
 }
 
 // Store post-collision population d of the cell at offset n into its
 // streamed position x + c_d.  With WALLS, a population whose target lies
 // beyond a wall returns into the cell as the opposite direction (halfway
 // bounce-back) with the moving-wall term -6 w_d rho_s (c_d . U_wall).
-template <typename T, bool WALLS>
-__device__ __forceinline__ void push_one(T *__restrict__ fdst, u32 S, int s, int d, float v, float rs, float r0s,
-                                         u32 n, bool bottom, bool top, float Uw, int LxLy, const int dxy[3][3]) {
+template <typename T, bool WALLS, int RX>
+__device__ __forceinline__ void push_one(T *__restrict__ fdst, u32 S, int s, int d, float v, float rs,
+                                         const PushOffsets &P, u32 n, bool bottom, bool top, float Uw, int LxLy,
+                                         const int dxy[3][3]) {
     int dir = d;
     u32 dst = n + (u32)(cz(d) * LxLy + dxy[cx(d) + 1][cy(d) + 1]);
+    bool wall = false;
     if (WALLS && ((cz(d) < 0 && bottom) || (cz(d) > 0 && top))) {
         v -= 6.f * wq(d) * rs * (float)cx(d) * (cz(d) < 0 ? -Uw : Uw);
         dir = opp(d);
         dst = n;
+        wall = true;
     }
-    if (Store<T>::offset) v -= wq(d) * r0s;
+    if (Store<T>::offset) v -= wq(d) * push_offset<RX>(P, s, d, wall);
     Store<T>::st(fdst + (u32)((s * Q + dir) * S + dst), v);
 }
 
@@ -236,10 +267,10 @@ __device__ __forceinline__ void push_one(T *__restrict__ fdst, u32 S, int s, int
 // its 19 populations.  Opposite directions share the symmetric parts:
 //   f^eq_{i,-i} = w rho (1 + 9/2 (c.u)^2 - 3/2 u.u) +- 3 w rho (c.u)
 //   S_{i,-i}    = (1 - 1/2tau) w (9 (c.u)(c.F) - 3 u.F) +- 3 (1 - 1/2tau) w (c.F)
-template <typename T, bool WALLS>
-__device__ __forceinline__ void collide_push(const float *fv, T *__restrict__ fdst, u32 S, int s, float rs, float r0s,
-                                             const float u[3], const float F[3], float om, u32 n, bool bottom,
-                                             bool top, float Uw, int LxLy, const int dxy[3][3]) {
+template <typename T, bool WALLS, int RX>
+__device__ __forceinline__ void collide_push(const float *fv, T *__restrict__ fdst, u32 S, int s, float rs,
+                                             const PushOffsets &P, const float u[3], const float F[3], float om, u32 n,
+                                             bool bottom, bool top, float Uw, int LxLy, const int dxy[3][3]) {
     const float omc = 1.0f - om, pref = 1.0f - 0.5f * om;
     const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     const float uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
@@ -247,7 +278,7 @@ __device__ __forceinline__ void collide_push(const float *fv, T *__restrict__ fd
     const float srcb = -3.f * uF * pref;           // (1 - 1/2tau)(-3 u.F)
     {
         float v = omc * fv[0] + wq(0) * (om * base0 + srcb);
-        if (Store<T>::offset) v -= wq(0) * r0s;
+        if (Store<T>::offset) v -= wq(0) * (P.track ? P.own[s] : P.r0[s]);
         Store<T>::st(fdst + (u32)(s * Q * S + n), v);
     }
 #pragma unroll
@@ -257,9 +288,9 @@ __device__ __forceinline__ void collide_push(const float *fv, T *__restrict__ fd
         const float cF = cx(i) * F[0] + cy(i) * F[1] + cz(i) * F[2];
         const float sym = w * (om * (base0 + 4.5f * rs * cu * cu) + srcb + 9.f * pref * cu * cF);
         const float anti = w * (om * 3.f * rs * cu + 3.f * pref * cF);
-        push_one<T, WALLS>(fdst, S, s, i, omc * fv[i] + (sym + anti), rs, r0s, n, bottom, top, Uw, LxLy, dxy);
-        push_one<T, WALLS>(fdst, S, s, i + 1, omc * fv[i + 1] + (sym - anti), rs, r0s, n, bottom, top, Uw, LxLy,
-                           dxy);
+        push_one<T, WALLS, RX>(fdst, S, s, i, omc * fv[i] + (sym + anti), rs, P, n, bottom, top, Uw, LxLy, dxy);
+        push_one<T, WALLS, RX>(fdst, S, s, i + 1, omc * fv[i + 1] + (sym - anti), rs, P, n, bottom, top, Uw, LxLy,
+                               dxy);
     }
 }
 
@@ -328,11 +359,16 @@ k_fused(const InstDev *__restrict__ insts, const int *__restrict__ item_off, int
             L.r3[0] = ring3(q - 1);
             L.r3[1] = ring3(q);
             L.r3[2] = ring3(q + 1);
-            L.c4[0] = ring4(q - 2);
-            L.c4[1] = ring4(q - 1);
-            L.c4[2] = ring4(q);
-            L.c4[3] = ring4(q + 1);
-            L.j2 = ring2(q);
+            L.ur[0] = ring3(q - 2);
+            L.ur[1] = L.r3[0];
+            L.ur[2] = L.r3[1];
+            L.cf[0] = ring4(q - 1);
+            L.cf[1] = ring4(q);
+            L.cf[2] = ring4(q + 1);
+            L.cu[0] = ring4(q - 2);
+            L.cu[1] = L.cf[0];
+            L.cu[2] = L.cf[1];
+            L.j3 = ring2(q);
 
             // ---------------- stage M(p): radius-2 region of plane clamp(p)
             {
@@ -342,8 +378,8 @@ k_fused(const InstDev *__restrict__ insts, const int *__restrict__ item_off, int
                     const int i = t + rr * NT;
                     if (rr * NT + NT <= R2N || i < R2N) {
                         MCell m;
-                        m_load<T>(I, fin, Cin, S, pl + om_ofs[rr], m);
-                        m_store<TY>(I, m, i, L.r3[2], ring2(p), L.c4[3]);
+                        m_load<T>(I, fin, Cin, S, pl + om_ofs[rr], cur, m);
+                        m_store<TY>(I, m, i, L.r3[2], ring2(p), L.cf[2]);
                     }
                 }
             }
@@ -358,15 +394,16 @@ k_fused(const InstDev *__restrict__ insts, const int *__restrict__ item_off, int
                     stage_f_cell<TY>(I, gy * RX + gx, L, a, b, uu, ra, rb);
                 }
             }
-            __syncthreads();
-            // ---------------- stage X(q): collision + push streaming
+            // ---------------- stage X(q): collision + push streaming (own cell only:
+            // needs no barrier after stage F)
             if (q >= z0 && q < z1 && valid) {
                 const u32 nq = (u32)(q * LxLy) + ofs_in;
+                const float2 od = offset_dens<T>(I, cur, nq);
                 float fx[2 * Q];
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
-                    fx[i] = ldpop(fin + (long long)i * S + nq, wq(i) * I.rho0[0]);
-                    fx[Q + i] = ldpop(fin + (long long)(Q + i) * S + nq, wq(i) * I.rho0[1]);
+                    fx[i] = ldpop(fin + (long long)i * S + nq, wq(i) * od.x);
+                    fx[Q + i] = ldpop(fin + (long long)(Q + i) * S + nq, wq(i) * od.y);
                 }
                 const float rt = rAo + rBo;
                 if (!(rt > 0.f) || uo[0] != uo[0] || uo[1] != uo[1] || uo[2] != uo[2])
@@ -374,18 +411,31 @@ k_fused(const InstDev *__restrict__ insts, const int *__restrict__ item_off, int
                 const float nu = (rAo * I.nu_A + rBo * I.nu_B) / rt;
                 const float om = 1.0f / (3.0f * nu + 0.5f);
                 const bool bottom = q == 0, top = q == Lz - 1;
-                collide_push<T, true>(fx, fout, S, 0, rAo, I.rho0[0], uo, FA, om, nq, bottom, top, Uw, LxLy, dxy);
-                collide_push<T, true>(fx + Q, fout, S, 1, rBo, I.rho0[1], uo, FB, om, nq, bottom, top, Uw, LxLy, dxy);
+                PushOffsets P;
+                const float2 *rho_s = reinterpret_cast<const float2 *>(smem() + Rg::RHO);
+                P.ring[0] = rho_s + L.r3[0] * R2N;
+                P.ring[1] = rho_s + L.r3[1] * R2N;
+                P.ring[2] = rho_s + L.r3[2] * R2N;
+                P.idx = idx_in;
+                P.own[0] = rAo;
+                P.own[1] = rBo;
+                P.track = I.dens[0] != nullptr;
+                P.r0[0] = I.rho0[0];
+                P.r0[1] = I.rho0[1];
+                collide_push<T, true, RX>(fx, fout, S, 0, rAo, P, uo, FA, om, nq, bottom, top, Uw, LxLy, dxy);
+                collide_push<T, true, RX>(fx + Q, fout, S, 1, rBo, P, uo, FB, om, nq, bottom, top, Uw, LxLy, dxy);
+                // this step's densities: the offsets of the state just written
+                if (Store<T>::offset && P.track) I.dens[cur][nq] = make_float2(rAo, rBo);
             }
+            __syncthreads();  // u of plane q complete on the radius-1 region
             // ---------------- stage U(r): FENE-P update, Eq. 2 (Eq. 4)
             if (r >= z0 && r < z1 && valid) {
-                // planes r-1, r, r+1 = q-2, q-1, q: u slots r3[2], r3[0], r3[1]
-                const float *um = smem() + Rg::U + L.r3[2] * 3 * R2N;
-                const float *uc = smem() + Rg::U + L.r3[0] * 3 * R2N;
-                const float *up = smem() + Rg::U + L.r3[1] * 3 * R2N;
-                const float *cm = smem() + Rg::C + L.c4[0] * 6 * R2N;
-                const float *cc = smem() + Rg::C + L.c4[1] * 6 * R2N;
-                const float *cp = smem() + Rg::C + L.c4[2] * 6 * R2N;
+                const float *um = smem() + Rg::U + L.ur[0] * 3 * R2N;
+                const float *uc = smem() + Rg::U + L.ur[1] * 3 * R2N;
+                const float *up = smem() + Rg::U + L.ur[2] * 3 * R2N;
+                const float *cm = smem() + Rg::C + L.cu[0] * 6 * R2N;
+                const float *cc = smem() + Rg::C + L.cu[1] * 6 * R2N;
+                const float *cp = smem() + Rg::C + L.cu[2] * 6 * R2N;
                 const int i0 = idx_in;
                 float u0[3], Gr[3][3];
 #pragma unroll
@@ -428,7 +478,7 @@ k_fused(const InstDev *__restrict__ insts, const int *__restrict__ item_off, int
                 }
                 if (!(c[0] + c[1] + c[2] < I.L2)) raise_flag(status, I, kFlagDiverged);
             }
-            __syncthreads();
+            __syncthreads();  // stage U done with the rings before stage M(p+1)
         }
     }
 }

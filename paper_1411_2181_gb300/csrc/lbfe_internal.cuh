@@ -71,7 +71,9 @@ struct InstDev {
     float G, Uw, nu_A, nu_B;         // Shan-Chen coupling, wall speed, solvent viscosities
     float pi_coef, L2, inv_tauP;     // eta_P/tau_P, L^2, 1/tau_P
     float gx, gy, gz;                // body acceleration
-    float rho0[2];                   // storage offsets
+    float rho0[2];                   // constant storage offsets (used when dens is null)
+    float2 *dens[2];                 // per-cell offset densities of the reduced forms, ping-pong:
+                                     // the state in f[c] is stored relative to w_i * dens[c ^ 1]
     int ntx, nty, nzc, zc;           // fused kernel: column tiles in x, y; z-chunks and their depth
     unsigned *status;                // this instance's status word (may be null)
 };
@@ -86,6 +88,18 @@ constexpr int kBlock = 256;          // threads per block of the cell-per-thread
 constexpr int kObsBlocks = 304;      // 2 x 152 SMs for the observables reduction
 
 __device__ __forceinline__ int wrapi(int a, int L) { return a < 0 ? a + L : (a >= L ? a - L : a); }
+
+// Offset densities (rho0_A, rho0_B) of cell n for the state held in f[cur]:
+// the reduced storage forms keep f_i - w_i rho0_s with rho0_s the cell's own
+// densities of the previous step (tracked per cell), so that the stored
+// value is the small deviation from the cell's rest equilibrium in either
+// phase; without tracking the constant offsets apply.  FP32 stores f.
+template <typename T>
+__device__ __forceinline__ float2 offset_dens(const InstDev &I, int cur, long long n) {
+    if (!Store<T>::offset) return make_float2(0.f, 0.f);
+    if (I.dens[0]) return __ldg(I.dens[cur ^ 1] + n);
+    return make_float2(I.rho0[0], I.rho0[1]);
+}
 
 // Instance owning block b of a tiled launch (tile_off[k] = first block of k).
 __device__ __forceinline__ int find_inst(const int *tile_off, int n, int b) {

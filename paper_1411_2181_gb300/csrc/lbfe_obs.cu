@@ -27,7 +27,6 @@ k_obs_planes(const InstDev *__restrict__ insts, int k, int cur, unsigned *status
     __syncthreads();
     const T *f = (const T *)I.f[cur];
     const long long S = I.S;
-    const float r0a = I.rho0[0], r0b = I.rho0[1];
     double mA = 0.0, mB = 0.0;
     bool bad = false;
     const int rows = Ly * Lz;
@@ -36,11 +35,12 @@ k_obs_planes(const InstDev *__restrict__ insts, int k, int cur, unsigned *status
         for (int x = threadIdx.x; x < Lx; x += blockDim.x) {
             const long long n = (long long)row * Lx + x;
             float ra = 0.f, rb = 0.f;
+            const float2 od = offset_dens<T>(I, cur, n);
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 float va = Store<T>::ld(f + (long long)i * S + n);
                 float vb = Store<T>::ld(f + (long long)(Q + i) * S + n);
-                if (Store<T>::offset) { va += wq(i) * r0a; vb += wq(i) * r0b; }
+                if (Store<T>::offset) { va += wq(i) * od.x; vb += wq(i) * od.y; }
                 ra += va;
                 rb += vb;
             }

@@ -18,7 +18,8 @@ Two search modes over held-out (De, lambda, 2R/W, phase) triples:
   mlp     - the network's break-up logit over a Ca grid gives Ca* and the
             bracket Ca* -/+ delta; both ends are verified by full runs (and
             the bracket is moved outwards until they are stable / broken),
-            then halved until the width is <= tol.
+            then halved until the width is <= tol.  A case predicted stable
+            (breaking) over the whole range is first run at that end only.
 Every verdict in both modes comes from a full simulation; the network only
 chooses which simulations to run.
 """
@@ -255,17 +256,28 @@ def search_mlp(triples, net, tol=0.02, delta=0.04, lo=CA_MIN, hi=CA_MAX, device=
     2 delta in that direction, until both ends hold.  Then it is halved."""
     stats = {"rounds": 0}
     grid = np.linspace(lo, hi, 341)
-    searches = []
+    searches, ok = [], {}
     for t in triples:
         X = features([_case(t, float(ca), 0) for ca in grid])
         logit = net.forward(X)[:, 2]
         above = np.nonzero(logit > 0)[0]
-        ca_star = float(grid[above[0]]) if len(above) else hi
-        searches.append(Search(t, max(lo, ca_star - delta), min(hi, ca_star + delta)))
-    ok = {id(s): [False, False] for s in searches}   # lower end stable / upper end broken verified
+        if len(above) == 0:
+            # predicted stable over the whole range: one run at the upper end
+            s = Search(t, hi, hi)
+            ok[id(s)] = [False, True]
+        elif above[0] == 0:
+            # predicted to break over the whole range: one run at the lower end
+            s = Search(t, lo, lo)
+            ok[id(s)] = [True, False]
+        else:
+            ca_star = float(grid[above[0]])
+            s = Search(t, max(lo, ca_star - delta), min(hi, ca_star + delta))
+            ok[id(s)] = [False, False]   # lower end stable / upper end broken verified
+        searches.append(s)
     pending = list(searches)
     while pending:
-        cas = [[e for e, done in ((s.lo, ok[id(s)][0]), (s.hi, ok[id(s)][1])) if not done] for s in pending]
+        cas = [sorted({e for e, done in ((s.lo, ok[id(s)][0]), (s.hi, ok[id(s)][1])) if not done})
+               for s in pending]
         res = _verdict_round(pending, cas, device, stats, seed)
         stats["rounds"] += 1
         nxt = []
@@ -273,6 +285,13 @@ def search_mlp(triples, net, tol=0.02, delta=0.04, lo=CA_MIN, hi=CA_MAX, device=
             f = ok[id(s)]
             r_lo = None if f[0] else res[(id(s), s.lo)]
             r_hi = None if f[1] else res[(id(s), s.hi)]
+            if s.lo == s.hi:                      # a single predicted end was run
+                if r_lo is False:                 # stable at the upper limit: Ca_cr >= hi
+                    f[0] = f[1] = True
+                    continue
+                if r_hi is True:                  # breaks at the lower limit: Ca_cr <= lo
+                    f[0] = f[1] = True
+                    continue
             if r_lo is True:                      # breaks at the lower end: Ca_cr is below it
                 s.hi, f[1] = s.lo, True
                 if s.lo <= lo:

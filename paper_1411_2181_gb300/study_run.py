@@ -42,27 +42,32 @@ def main(argv=None):
     ap.add_argument("--delta", type=float, default=0.06)
     ap.add_argument("--out", default=None)
     ap.add_argument("--params-out", default=None)
+    ap.add_argument("--params-in", default=None, help="reuse a trained network (skips the training runs)")
     a = ap.parse_args(argv)
 
     report = {}
-    st_train = {}
     t0 = time.perf_counter()
-    cases, verdicts = study.training_set(a.train, seed=100, stats=st_train)
-    report["training_runs"] = dict(st_train, valid=len(cases), broken=int(sum(v.broken for v in verdicts)))
-    X = study.features(cases)
-    T, M = study.targets(verdicts)
-    # hold out 1/8 of the runs to estimate the network's accuracy
-    n_val = max(1, len(X) // 8)
-    net = mlp.MLP(max_batch=max(4096, len(X)), bf16=True)
-    net.set_params(mlp.init_params(0))
-    t1 = time.perf_counter()
-    hist = net.fit(X[n_val:], T[n_val:], M[n_val:], epochs=a.epochs, lr=3e-3, batch=256)
-    train_s = time.perf_counter() - t1
-    yv = net.forward(X[:n_val])
-    acc = float(np.mean((yv[:, 2] > 0) == (T[:n_val, 2] > 0.5)))
-    d_err = float(np.sqrt(np.sum(M[:n_val] * (yv[:, 0] - T[:n_val, 0]) ** 2) / max(1.0, M[:n_val].sum())))
-    report["network"] = {"epochs": a.epochs, "final_loss": hist[-1], "first_loss": hist[0],
-                         "train_seconds": train_s, "val_breakup_accuracy": acc, "val_D_rmse": d_err}
+    net = mlp.MLP(max_batch=max(4096, a.train), bf16=True)
+    if a.params_in:
+        net.set_params(np.load(a.params_in))
+        report["network"] = {"loaded": a.params_in}
+    else:
+        st_train = {}
+        cases, verdicts = study.training_set(a.train, seed=100, stats=st_train)
+        report["training_runs"] = dict(st_train, valid=len(cases), broken=int(sum(v.broken for v in verdicts)))
+        X = study.features(cases)
+        T, M = study.targets(verdicts)
+        # hold out 1/8 of the runs to estimate the network's accuracy
+        n_val = max(1, len(X) // 8)
+        net.set_params(mlp.init_params(0))
+        t1 = time.perf_counter()
+        hist = net.fit(X[n_val:], T[n_val:], M[n_val:], epochs=a.epochs, lr=3e-3, batch=256)
+        train_s = time.perf_counter() - t1
+        yv = net.forward(X[:n_val])
+        acc = float(np.mean((yv[:, 2] > 0) == (T[:n_val, 2] > 0.5)))
+        d_err = float(np.sqrt(np.sum(M[:n_val] * (yv[:, 0] - T[:n_val, 0]) ** 2) / max(1.0, M[:n_val].sum())))
+        report["network"] = {"epochs": a.epochs, "final_loss": hist[-1], "first_loss": hist[0],
+                             "train_seconds": train_s, "val_breakup_accuracy": acc, "val_D_rmse": d_err}
     if a.params_out:
         np.save(a.params_out, net.get_params())
 
@@ -70,16 +75,18 @@ def main(argv=None):
     sb, stb = study.search_bisect(triples)
     sm, stm = study.search_mlp(triples, net, delta=a.delta)
     per = []
-    agree = 0
+    agree = overlap = 0
     for b, m in zip(sb, sm):
         cb, cm = 0.5 * (b.lo + b.hi), 0.5 * (m.lo + m.hi)
         agree += abs(cb - cm) <= 0.01 + 1e-9
+        overlap += max(b.lo, m.lo) <= min(b.hi, m.hi) + 1e-12
         per.append({"triple": b.triple, "bisect": [b.lo, b.hi, b.runs], "mlp": [m.lo, m.hi, m.runs]})
     keys = ("runs", "rounds", "seconds", "lattice_updates", "diverged")
     report["bisect"] = {k: stb.get(k, 0) for k in keys}
     report["mlp"] = {k: stm.get(k, 0) for k in keys}
     report["in_range"] = int(sum(CA_IN(b) for b in sb))
     report["agree_within_0.01"] = f"{agree}/{len(triples)}"
+    report["brackets_consistent"] = f"{overlap}/{len(triples)}"
     report["per_triple"] = per
     report["total_seconds"] = time.perf_counter() - t0
     txt = json.dumps(report, indent=1)

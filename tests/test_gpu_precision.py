@@ -1,0 +1,58 @@
+"""Populations stored as FP16 / BF16 offsets from each cell's previous
+densities, FP32 arithmetic: deformation, orientation and mass against the
+FP32 path and the FP64 oracle on the 64^3 reduced run of the strongly
+confined viscoelastic-droplet workload (R = 22, W = 64, lambda = 3, De = 2,
+L^2 = 400)."""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1411_2181_gb300 import configs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1411_2181_gb300 import build
+    build.build()
+    from paper_1411_2181_gb300 import lbfe
+    return lbfe
+
+
+def trajectory(L, prec, steps, every):
+    p, rho, _ = configs.config3(crop=True)
+    s = L.Solver(replace(p, precision=prec))
+    s.init(0, rho)
+    out = [s.observables(0)]
+    for _ in range(steps // every):
+        s.step(every)
+        out.append(s.observables(0))
+    return out
+
+
+@pytest.fixture(scope="module")
+def runs(L):
+    return {prec: trajectory(L, prec, 1500, 300) for prec in (0, 1, 2)}
+
+
+def test_fp32_observables_match_oracle(L, runs):
+    p, rho, _ = configs.config3(crop=True)
+    o = O.Oracle(p.oracle_dict(), rho)
+    o.step(300)
+    ro = o.observables()
+    g = runs[0][1]
+    assert abs(g["D"] - ro["D"]) < 1e-6 and abs(g["theta_deg"] - ro["theta_deg"]) < 1e-3
+
+
+@pytest.mark.parametrize("prec,tol_D,tol_theta,tol_mass", [(1, 1e-3, 0.05, 1e-4), (2, 5e-3, 0.5, 1e-3)])
+def test_reduced_storage_errors(runs, prec, tol_D, tol_theta, tol_mass):
+    ref, red = runs[0], runs[prec]
+    dD = max(abs(a["D"] - b["D"]) for a, b in zip(ref, red))
+    dth = max(abs(a["theta_deg"] - b["theta_deg"]) for a, b in zip(ref[1:], red[1:]))
+    m0 = np.array(red[0]["mass"])
+    dm = max((np.abs(np.array(r["mass"]) - m0) / m0).max() for r in red)
+    print(f"precision {prec}: max |dD| {dD:.2e}, max |dtheta| {dth:.3f} deg, mass drift {dm:.2e}")
+    assert dD < tol_D and dth < tol_theta and dm < tol_mass

@@ -1,0 +1,94 @@
+"""Host logic of the Ca_cr searches with a stand-in verdict (no GPU): the
+verdict of a case is 'broken' iff Ca exceeds a known threshold that depends
+on the triple, so both modes must bracket that threshold within the
+tolerance, and the proposal mode must spend fewer runs when its guess is
+close."""
+import numpy as np
+import pytest
+
+from paper_1411_2181_gb300 import study
+
+
+def fake_threshold(c):
+    De, lam, conf, phase = c.De, c.lam, c.conf, c.phase
+    return 1.0 + 0.3 * conf + 0.1 * De - 0.2 * (phase == 2) + 0.05 * lam
+
+
+@pytest.fixture
+def fake_runs(monkeypatch):
+    calls = []
+
+    def run_batch(cases, device=None, stats=None):
+        calls.append(len(cases))
+        if stats is not None:
+            stats["runs"] = stats.get("runs", 0) + len(cases)
+            stats["seconds"] = stats.get("seconds", 0.0)
+            stats["lattice_updates"] = 0
+        return [study.Verdict(c.Ca > fake_threshold(c), 0.1, 30.0, 0, float("nan")) for c in cases]
+
+    monkeypatch.setattr(study, "run_batch", run_batch)
+    return calls
+
+
+TRIPLES = [(0.0, 1.0, 0.65, 1), (2.0, 0.5, 0.75, 2), (1.0, 1.0, 0.7, 2), (0.5, 0.5, 0.62, 1)]
+
+
+def test_bisection_brackets_threshold(fake_runs):
+    searches, stats = study.search_bisect(TRIPLES, tol=0.02)
+    for s in searches:
+        th = fake_threshold(study._case(s.triple, 0.0, 0))
+        assert s.lo <= th < s.hi and s.width <= 0.02
+    # 2 checks + ceil(log2(1.7 / 0.02)) = 7 halvings per triple
+    assert all(s.runs == 9 for s in searches)
+    assert stats["rounds"] == 8
+
+
+class FakeNetwork:
+    """A proposal network stand-in whose logit crosses 0 at the threshold
+    plus an offset (the network's error)."""
+
+    def __init__(self, offset):
+        self.offset = offset
+
+    def forward(self, X):
+        ca = X[:, 0] * 0.6 + 1.2
+        cases = [study.Case(Ca=0.0, De=float(x[1] + 1.0), lam=float(np.exp(x[2] * np.log(2.0))),
+                            conf=float(x[3] * 0.1 + 0.7), phase=1 if x[5] < 0 else 2) for x in X]
+        th = np.array([fake_threshold(c) for c in cases]) + self.offset
+        y = np.zeros((len(X), 4), np.float32)
+        y[:, 2] = (ca - th) * 10
+        return y
+
+
+@pytest.mark.parametrize("offset", [0.0, 0.03, -0.05, 0.2, 5.0, -5.0])
+def test_proposal_mode_brackets_threshold(fake_runs, offset):
+    searches, stats = study.search_mlp(TRIPLES, FakeNetwork(offset), tol=0.02, delta=0.06)
+    for s in searches:
+        th = fake_threshold(study._case(s.triple, 0.0, 0))
+        assert s.lo <= th < s.hi and s.width <= 0.02
+        # the lower end was verified stable and the upper end broken
+        lows = [ca for ca, br in s.history if not br]
+        highs = [ca for ca, br in s.history if br]
+        assert max(lows) == pytest.approx(s.lo) and min(highs) == pytest.approx(s.hi)
+
+
+def test_proposal_saves_runs_when_close(fake_runs):
+    sb, _ = study.search_bisect(TRIPLES, tol=0.02)
+    sm, stm = study.search_mlp(TRIPLES, FakeNetwork(0.01), tol=0.02, delta=0.06)
+    assert sum(s.runs for s in sm) < sum(s.runs for s in sb)
+    for b, m in zip(sb, sm):
+        assert abs(0.5 * (b.lo + b.hi) - 0.5 * (m.lo + m.hi)) <= 0.02
+
+
+def test_features_scaling():
+    c = study.Case(Ca=1.2, De=1.0, lam=1.0, conf=0.7, L2=200.0, phase=1)
+    x = study.features([c])[0]
+    assert np.allclose(x, [0, 0, 0, 0, 0, -1], atol=1e-6)
+
+
+def test_range_ends_need_one_run_when_predicted(fake_runs):
+    """A network predicting stability over the whole range spends one run to
+    confirm it (the threshold lies above the range here)."""
+    searches, _ = study.search_mlp(TRIPLES, FakeNetwork(5.0), tol=0.02, delta=0.06, hi=1.0)
+    for s in searches:
+        assert s.lo == s.hi == 1.0 and s.runs == 1
