@@ -171,7 +171,9 @@ lbfe_status lbfe_check(lbfe_handle *h);
 lbfe_status lbfe_get_field(lbfe_handle *h, int k, int which, void *host_dst, size_t bytes);
 lbfe_status lbfe_set_field(lbfe_handle *h, int k, int which, const void *host_src, size_t bytes);
 
-/* Number of kernel launches one lbfe_step(h, 1) enqueues. */
+/* Number of kernel launches one lbfe_step(h, 1) enqueues: one per group of
+ * up to 64 instances (the step kernel carries the instance descriptors in
+ * its parameter space). */
 int lbfe_launches_per_step(const lbfe_handle *h);
 
 /* Launch shape of the step kernel: column-tile height tile_y in {4, 8, 16}

@@ -213,6 +213,8 @@ struct lbfe_handle {
     int *tile_off = nullptr;
     int total_tiles = 0;
     int *item_off = nullptr;
+    std::vector<int> item_off_h;
+    std::vector<lbfe::PopMaps> maps;
     int total_items = 0, fused_grid = 0, tile_y = 8, z_chunk_req = 0, num_sms = 0, blocks_per_sm = 0;
     unsigned *status = nullptr;
     double *mass = nullptr;
@@ -229,6 +231,9 @@ struct lbfe_handle {
         c.status = status;
         c.stream = stream;
         c.item_off = item_off;
+        c.item_off_host = item_off_h.data();
+        c.maps_host = maps.empty() ? nullptr : maps.data();
+        c.fused_slots = num_sms * blocks_per_sm;
         c.total_items = total_items;
         c.fused_grid = fused_grid;
         c.tile_y = tile_y;
@@ -275,6 +280,12 @@ static lbfe_status configure_fused(lbfe_handle *h, int tile_y, int z_chunk) {
     h->z_chunk_req = z_chunk;
     h->blocks_per_sm = bps;
     h->total_items = off[h->n];
+    h->item_off_h = off;
+    h->maps.assign(h->n, lbfe::PopMaps{});
+    for (int k = 0; k < h->n; ++k) {
+        e = lbfe::fused_pop_maps(h->inst[k], h->precision, tile_y, &h->maps[k]);
+        if (e != cudaSuccess) return cuda_fail(e, "fused_pop_maps");
+    }
     h->fused_grid = (int)std::min<long long>(h->total_items, slots);
     e = cudaMemcpyAsync(h->inst_dev, h->inst.data(), sizeof(InstDev) * h->n, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->item_off, off.data(), sizeof(int) * (h->n + 1), cudaMemcpyHostToDevice, h->stream);
@@ -455,6 +466,7 @@ lbfe_status lbfe_check(lbfe_handle *h) {
     unsigned st = 0;
     CK(cudaMemcpyAsync(&st, h->status, sizeof st, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    if (st & lbfe::kFlagTimeout) return LBFE_ERR_TIMEOUT;
     return (st & lbfe::kFlagDiverged) ? LBFE_ERR_DIVERGED : LBFE_OK;
 }
 
@@ -623,7 +635,7 @@ lbfe_status lbfe_set_field(lbfe_handle *h, int k, int which, const void *host_sr
     }
 }
 
-int lbfe_launches_per_step(const lbfe_handle *h) { return h ? 1 : 0; }
+int lbfe_launches_per_step(const lbfe_handle *h) { return h ? lbfe::fused_launches(h->n) : 0; }
 
 lbfe_status lbfe_tune(lbfe_handle *h, int tile_y, int z_chunk) {
     if (!h) return LBFE_ERR_BAD_PARAM;

@@ -26,23 +26,211 @@
 // stage U needs) and after stage U.
 // Planes beyond a wall are loaded as the adjacent plane (mirror ghosts of
 // rho, C and Pi); the velocity ghost 2 U_wall - u is applied in stage U.
+//
+// Blackwell specifics.
+//  * The tile's own 32 x TY populations of the next plane arrive by one TMA
+//    tensor copy (box 32 x TY x 1 x 38 of the (x, y, z, population) view)
+//    into a shared-memory staging buffer, issued as soon as stage M has
+//    consumed the buffer: the DRAM reads of plane p+1 overlap stages F, X
+//    and U of plane p.  Completion is tracked by an mbarrier with a bounded
+//    wait.  The radius-2 halo (recomputed) and ragged-tile cells are read
+//    with ordinary loads.
+//  * Each thread's own-cell populations, decoded to FP32 in stage M(p), wait
+//    in tensor memory (TMEM) for the collision X(p) one plane later: two
+//    plane buffers of 38 columns per warp in the warp's 32-lane quarter,
+//    written and read with tcgen05.st / tcgen05.ld.  The collision therefore
+//    issues no global loads, and the register file does not hold the
+//    populations across the stencil stages.
+//  * The instance descriptors travel in the kernel parameter space (up to
+//    64 instances per launch): scalars and pointers come from the constant
+//    bank instead of per-use global loads.
+#include <cstring>
+#include <mutex>
+
 #include "lbfe_internal.cuh"
 
 namespace lbfe {
 
 namespace {
 
+typedef unsigned int u32;
+
 template <int TY>
 struct Geom {
     static constexpr int TX = 32;
     static constexpr int NT = TX * TY;                 // threads = tile cells
+    static constexpr int WARPS = NT / 32;
     static constexpr int RX = TX + 4, RY = TY + 4;     // radius-2 region
     static constexpr int R2N = RX * RY;
     static constexpr int NRING1 = 2 * (RX - 2) + 2 * TY;  // radius-1 cells outside the tile
+    static constexpr int NRING2 = 4 * TX + 4 * RY;        // radius-2 region cells outside the tile
+    static constexpr int MH = (NRING2 + NT - 1) / NT;     // stage-M halo rounds per thread
     // rings: rho (float2) x3, stress scalars (a f, a) x3, j 3x2, C 6x4, u 3x3
     static constexpr int FLOATS = (2 * 3 + 2 * 3 + 6 + 24 + 9) * R2N;
+    // TMEM: per warp two plane buffers in 64-column slots; warps w, w+4, ...
+    // share the lane quarter w % 4 and take consecutive 128-column ranges
+    static constexpr int TMEM_COLS = (WARPS / 4) * 128;
+    static_assert(WARPS % 4 == 0 && TMEM_COLS >= 32 && TMEM_COLS <= 512, "TMEM layout");
 };
 
+// ---------------------------------------------------------------- descriptors
+constexpr int kStepMaxInst = 64;
+
+// Per-instance descriptor of one launch (kernel parameter space).
+struct StepInst {
+    CUtensorMap pop_map;           // (x, y, z, population) view of fin, box 32 x TY x 1 x 38 (when tma)
+    int tma;                       // own-tile populations by TMA
+    int Lx, Ly, Lz, LxLy;
+    int visc_comp, ntx, nty, zc;   // visc_comp: 0 (A), 1 (B), -1 Newtonian
+    u32 S, pad_;                   // field stride
+    const void *fin;               // populations read (state t)
+    void *fout;                    // populations written (state t + 1)
+    const float *Cin;
+    float *Cout;
+    const float2 *dens_in;         // offsets of the state read (reduced forms with tracking, else null)
+    float2 *dens_out;              // offsets of the state written
+    unsigned *status;              // per-instance status word (may be null)
+    float G, Uw, nu_A, nu_B, pi_coef, L2, inv_tauP, gx, gy, gz, rho0A, rho0B;
+};
+
+// One launch covers up to kStepMaxInst instances.  A single instance takes
+// the same kernel as a batch, so that batching never changes the arithmetic
+// (the results of an instance are bitwise the same alone or in a batch).
+struct StepArgs {
+    int n, total_items;
+    unsigned *status;              // status word of the launch
+    int item_off[kStepMaxInst + 1];  // first work item of each instance
+    StepInst inst[kStepMaxInst];
+};
+
+__device__ __forceinline__ void raise_step_flag(unsigned *global, const StepInst &I, unsigned flag) {
+    atomicOr(global, flag);
+    if (I.status) atomicOr(I.status, flag);
+}
+
+// ---------------------------------------------------------------- TMEM access
+__device__ __forceinline__ u32 smem_addr(const void *p) { return (u32)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tm_alloc(u32 *dst, u32 ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tm_dealloc(u32 taddr, u32 ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tm_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// ---------------------------------------------------------------- TMA + mbarrier
+constexpr int kWaitLimit = 1 << 22;   // try_wait rounds before a wait is declared expired
+
+__device__ __forceinline__ void mbar_init(u32 bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// One thread: arm the barrier for `bytes` and start the copy of the box at
+// (x, y, z, 0) into shared memory at dst.
+__device__ __forceinline__ void tma_pop_box(const CUtensorMap *map, u32 dst, u32 bar, u32 bytes, int x, int y, int z) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(0), "r"(bar)
+        : "memory");
+}
+// Wait for the completion of phase `parity`; false once the limit expired.
+__device__ __forceinline__ bool mbar_wait(u32 bar, u32 parity) {
+    for (int it = 0; it < kWaitLimit; ++it) {
+        u32 ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tm_st32(u32 taddr, const float *v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};"
+                 :: "r"(taddr),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+                 "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+                 "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+                 "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])),
+                 "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])), "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])),
+                 "r"(__float_as_uint(v[20])), "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
+                 "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])), "r"(__float_as_uint(v[27])),
+                 "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])), "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+                 );
+}
+__device__ __forceinline__ void tm_st4(u32 taddr, const float *v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};"
+                 :: "r"(taddr),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3]))
+                 );
+}
+__device__ __forceinline__ void tm_st2(u32 taddr, const float *v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};"
+                 :: "r"(taddr),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1]))
+                 );
+}
+__device__ __forceinline__ void tm_ld32(u32 taddr, u32 *r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                 : 
+                   "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                   "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                   "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tm_ld4(u32 taddr, u32 *r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tm_ld2(u32 taddr, u32 *r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
+                 : "=r"(r[0]), "=r"(r[1])
+                 : "r"(taddr));
+}
+// Completes the loads above; the registers pass through the statement so
+// that no use of them can be scheduled before the wait.
+__device__ __forceinline__ void tm_wait_ld38(u32 *r) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 :
+                 "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]),
+                 "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
+                 "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]),
+                 "+r"(r[32]), "+r"(r[33]), "+r"(r[34]), "+r"(r[35]), "+r"(r[36]), "+r"(r[37])
+                 );
+}
+
+// The 38 populations of a cell: columns [0, 38) of a plane buffer.
+__device__ __forceinline__ void tm_store38(u32 taddr, const float *v) {
+    tm_st32(taddr, v);
+    tm_st4(taddr + 32, v + 32);
+    tm_st2(taddr + 36, v + 36);
+}
+__device__ __forceinline__ void tm_load38(u32 taddr, float *v) {
+    u32 r[38];
+    tm_wait_st();
+    tm_ld32(taddr, r);
+    tm_ld4(taddr + 32, r + 32);
+    tm_ld2(taddr + 36, r + 36);
+    tm_wait_ld38(r);
+#pragma unroll
+    for (int i = 0; i < 38; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ---------------------------------------------------------------- rings
 // Ring slot of plane p (p >= -4) in rings of 2, 3 and 4 planes.
 __device__ __forceinline__ int ring2(int p) { return (p + 12) & 1; }
 __device__ __forceinline__ int ring3(int p) { return (p + 12) % 3; }
@@ -61,7 +249,7 @@ __device__ __forceinline__ float ldpop(const T *p, float add) {
     return v;
 }
 
-// Ring cell h (0 <= h < NRING1) of the radius-1 region.
+// Cell h (0 <= h < NRING1) of the radius-1 region outside the tile.
 template <int TY>
 __device__ __forceinline__ void ring1_coord(int h, int &gx, int &gy) {
     using Gm = Geom<TY>;
@@ -77,7 +265,22 @@ __device__ __forceinline__ void ring1_coord(int h, int &gx, int &gy) {
     }
 }
 
-typedef unsigned int u32;
+// Cell h (0 <= h < NRING2) of the radius-2 region outside the tile: first
+// the four halo rows over the tile's own 32 columns (one aligned row per
+// warp), then the two-column strips left and right of the tile, row by row.
+template <int TY>
+__device__ __forceinline__ void ring2_coord(int h, int &gx, int &gy) {
+    if (h < 128) {
+        const int r = h >> 5;
+        gy = r < 2 ? r : TY + r;   // rows 0, 1, TY + 2, TY + 3
+        gx = 2 + (h & 31);
+    } else {
+        const int j = h - 128;
+        gy = j >> 2;               // 0 .. TY + 3
+        const int c = j & 3;
+        gx = c < 2 ? c : 32 + c;   // columns 0, 1, 34, 35
+    }
+}
 
 // Shared-memory rings (offsets in floats from the dynamic shared base):
 //   rho  float2 [3][R2N]          densities rho_A, rho_B
@@ -94,7 +297,8 @@ struct Ring {
 extern __shared__ float4 lbfe_smem4[];
 __device__ __forceinline__ float *smem() { return reinterpret_cast<float *>(lbfe_smem4); }
 
-// Stage M inputs of one cell: its 38 populations and 6 conformation components.
+// Stage M inputs of one cell: its 38 populations (decoded to FP32) and 6
+// conformation components.
 struct MCell {
     float f[2 * Q];
     float c[6];
@@ -103,10 +307,19 @@ struct MCell {
 // Cell offsets are 32-bit: an instance holds at most 2^26 cells, so every
 // field offset (s*19 + i)*S + n stays below 2^32.
 template <typename T>
-__device__ __forceinline__ void m_load(const InstDev &I, const T *__restrict__ fin, const float *__restrict__ Cin,
-                                       u32 S, u32 n, int cur, MCell &m) {
-    const float2 od = offset_dens<T>(I, cur, n);
-    const float ra0 = od.x, rb0 = od.y;
+__device__ __forceinline__ void m_load(const StepInst &I, const T *__restrict__ fin, const float *__restrict__ Cin,
+                                       u32 S, u32 n, MCell &m) {
+    float ra0 = 0.f, rb0 = 0.f;
+    if (Store<T>::offset) {
+        if (I.dens_in) {
+            const float2 od = __ldg(I.dens_in + n);
+            ra0 = od.x;
+            rb0 = od.y;
+        } else {
+            ra0 = I.rho0A;
+            rb0 = I.rho0B;
+        }
+    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         m.f[i] = ldpop(fin + (u32)(i * S + n), wq(i) * ra0);
@@ -116,10 +329,39 @@ __device__ __forceinline__ void m_load(const InstDev &I, const T *__restrict__ f
     for (int k = 0; k < 6; ++k) m.c[k] = __ldg(Cin + (u32)(k * S + n));
 }
 
+// As m_load, with the populations taken from the TMA staging buffer
+// (element (x, y, i) of the box at i * NT + y * 32 + x).
+template <typename T, int NT>
+__device__ __forceinline__ void m_load_staged(const StepInst &I, const T *stage, int t,
+                                              const float *__restrict__ Cin, u32 S, u32 n, MCell &m) {
+    float ra0 = 0.f, rb0 = 0.f;
+    if (Store<T>::offset) {
+        if (I.dens_in) {
+            const float2 od = __ldg(I.dens_in + n);
+            ra0 = od.x;
+            rb0 = od.y;
+        } else {
+            ra0 = I.rho0A;
+            rb0 = I.rho0B;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        m.f[i] = Store<T>::ld_plain(stage + i * NT + t);
+        m.f[Q + i] = Store<T>::ld_plain(stage + (Q + i) * NT + t);
+        if (Store<T>::offset) {
+            m.f[i] += wq(i) * ra0;
+            m.f[Q + i] += wq(i) * rb0;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) m.c[k] = __ldg(Cin + (u32)(k * S + n));
+}
+
 // Stage M for one cell: moments, stress scalars and conformation into the
 // ring slots of its plane.
 template <int TY>
-__device__ __forceinline__ void m_store(const InstDev &I, const MCell &m, int idx, int s3, int s2, int s4) {
+__device__ __forceinline__ void m_store(const StepInst &I, const MCell &m, int idx, int s3, int s2, int s4) {
     // s3: rho / stress slot, s2: j slot, s4: C slot of the plane
     constexpr int R2N = Geom<TY>::R2N;
     using Rg = Ring<TY>;
@@ -167,7 +409,7 @@ struct Slots {
 // velocity.  Writes u to the ring; returns the per-component total forces,
 // u and the densities.
 template <int TY>
-__device__ __forceinline__ void stage_f_cell(const InstDev &I, int idx, const Slots &L, float FA[3], float FB[3],
+__device__ __forceinline__ void stage_f_cell(const StepInst &I, int idx, const Slots &L, float FA[3], float FB[3],
                                              float u[3], float &rA, float &rB) {
     constexpr int R2N = Geom<TY>::R2N, RX = Geom<TY>::RX;
     using Rg = Ring<TY>;
@@ -243,17 +485,16 @@ __device__ __forceinline__ float push_offset(const PushOffsets &P, int s, int d,
 }
 
 // Store post-collision population d of the cell at offset n into its
-// streamed position x + c_d.  With WALLS, a population whose target lies
-// beyond a wall returns into the cell as the opposite direction (halfway
+// streamed position x + c_d.  A population whose target lies beyond a wall returns into the cell as the opposite direction (halfway
 // bounce-back) with the moving-wall term -6 w_d rho_s (c_d . U_wall).
-template <typename T, bool WALLS, int RX>
+template <typename T, int RX>
 __device__ __forceinline__ void push_one(T *__restrict__ fdst, u32 S, int s, int d, float v, float rs,
                                          const PushOffsets &P, u32 n, bool bottom, bool top, float Uw, int LxLy,
                                          const int dxy[3][3]) {
     int dir = d;
     u32 dst = n + (u32)(cz(d) * LxLy + dxy[cx(d) + 1][cy(d) + 1]);
     bool wall = false;
-    if (WALLS && ((cz(d) < 0 && bottom) || (cz(d) > 0 && top))) {
+    if ((cz(d) < 0 && bottom) || (cz(d) > 0 && top)) {
         v -= 6.f * wq(d) * rs * (float)cx(d) * (cz(d) < 0 ? -Uw : Uw);
         dir = opp(d);
         dst = n;
@@ -267,66 +508,131 @@ __device__ __forceinline__ void push_one(T *__restrict__ fdst, u32 S, int s, int
 // its 19 populations.  Opposite directions share the symmetric parts:
 //   f^eq_{i,-i} = w rho (1 + 9/2 (c.u)^2 - 3/2 u.u) +- 3 w rho (c.u)
 //   S_{i,-i}    = (1 - 1/2tau) w (9 (c.u)(c.F) - 3 u.F) +- 3 (1 - 1/2tau) w (c.F)
-template <typename T, bool WALLS, int RX>
+// so that with E = omega rho (1 - 3/2 u.u) - 3 (1 - 1/2tau) u.F the
+// post-collision pair is (1 - omega) f_{i,-i} + sym +- anti,
+//   sym  = w E + (c.u) (9/2 omega rho w (c.u) + 9 (1 - 1/2tau) w (c.F)),
+//   anti = 3 omega rho w (c.u) + 3 (1 - 1/2tau) w (c.F),
+// with the weight products formed once per weight class.
+template <typename T, int RX>
 __device__ __forceinline__ void collide_push(const float *fv, T *__restrict__ fdst, u32 S, int s, float rs,
                                              const PushOffsets &P, const float u[3], const float F[3], float om, u32 n,
                                              bool bottom, bool top, float Uw, int LxLy, const int dxy[3][3]) {
     const float omc = 1.0f - om, pref = 1.0f - 0.5f * om;
     const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     const float uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
-    const float base0 = rs * (1.f - 1.5f * uu);   // rho (1 - 3/2 u.u)
-    const float srcb = -3.f * uF * pref;           // (1 - 1/2tau)(-3 u.F)
+    const float E = om * (rs * (1.f - 1.5f * uu)) - 3.f * pref * uF;
+    const float a1 = 4.5f * om * rs, b1 = 9.f * pref, a2 = 3.f * om * rs, b2 = 3.f * pref;
     {
-        float v = omc * fv[0] + wq(0) * (om * base0 + srcb);
+        float v = omc * fv[0] + wq(0) * E;
         if (Store<T>::offset) v -= wq(0) * (P.track ? P.own[s] : P.r0[s]);
         Store<T>::st(fdst + (u32)(s * Q * S + n), v);
     }
+    // weight classes: faces (i = 1..6) and edges (i = 7..18)
+    float Ew[2], a1w[2], b1w[2], a2w[2], b2w[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const float w = wq(c == 0 ? 1 : 7);
+        Ew[c] = w * E;
+        a1w[c] = w * a1;
+        b1w[c] = w * b1;
+        a2w[c] = w * a2;
+        b2w[c] = w * b2;
+    }
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {
-        const float w = wq(i);
+        const int c = i <= 6 ? 0 : 1;
         const float cu = cx(i) * u[0] + cy(i) * u[1] + cz(i) * u[2];
         const float cF = cx(i) * F[0] + cy(i) * F[1] + cz(i) * F[2];
-        const float sym = w * (om * (base0 + 4.5f * rs * cu * cu) + srcb + 9.f * pref * cu * cF);
-        const float anti = w * (om * 3.f * rs * cu + 3.f * pref * cF);
-        push_one<T, WALLS, RX>(fdst, S, s, i, omc * fv[i] + (sym + anti), rs, P, n, bottom, top, Uw, LxLy, dxy);
-        push_one<T, WALLS, RX>(fdst, S, s, i + 1, omc * fv[i + 1] + (sym - anti), rs, P, n, bottom, top, Uw, LxLy,
-                               dxy);
+        const float sym = fmaf(cu, fmaf(a1w[c], cu, b1w[c] * cF), Ew[c]);
+        const float anti = fmaf(a2w[c], cu, b2w[c] * cF);
+        push_one<T, RX>(fdst, S, s, i, fmaf(omc, fv[i], sym + anti), rs, P, n, bottom, top, Uw, LxLy, dxy);
+        push_one<T, RX>(fdst, S, s, i + 1, fmaf(omc, fv[i + 1], sym - anti), rs, P, n, bottom, top, Uw,
+                               LxLy, dxy);
     }
 }
 
 }  // namespace
 
+// Position of work item `item`: instance, column tile and z-chunk.
+struct ItemPos {
+    int k, bx, by, z0, z1;
+};
+
+template <int TY>
+__device__ __forceinline__ ItemPos item_pos(const StepArgs &A, int item) {
+    ItemPos P;
+    P.k = 0;
+    for (int hi = A.n - 1; P.k < hi;) {
+        const int mid = (P.k + hi + 1) >> 1;
+        if (A.item_off[mid] <= item) P.k = mid; else hi = mid - 1;
+    }
+    const StepInst &I = A.inst[P.k];
+    int local = item - A.item_off[P.k];
+    P.bx = local % I.ntx;
+    local /= I.ntx;
+    P.by = local % I.nty;
+    P.z0 = (local / I.nty) * I.zc;
+    P.z1 = min(I.Lz, P.z0 + I.zc);
+    return P;
+}
+
+template <int TY>
+__device__ __forceinline__ void issue_plane(const StepArgs &A, const ItemPos &P, int plane, u32 dst, u32 bar,
+                                            u32 bytes) {
+    const StepInst &I = A.inst[P.k];
+    tma_pop_box(&I.pop_map, dst, bar, bytes, P.bx * 32, P.by * TY, min(max(plane, 0), I.Lz - 1));
+}
+
 template <typename T, int TY>
 __global__ void __launch_bounds__(32 * TY, TY >= 16 ? 1 : (TY >= 8 ? 2 : 3))
-k_fused(const InstDev *__restrict__ insts, const int *__restrict__ item_off, int n_inst, int total_items,
-        int cur, unsigned *status) {
+k_fused(const __grid_constant__ StepArgs A) {
     using Gm = Geom<TY>;
-    constexpr int TX = Gm::TX, NT = Gm::NT, RX = Gm::RX, RY = Gm::RY, R2N = Gm::R2N;
-    constexpr int MR = (R2N + NT - 1) / NT;   // stage-M rounds per thread
+    constexpr int TX = Gm::TX, NT = Gm::NT, RX = Gm::RX, RY = Gm::RY, R2N = Gm::R2N, MH = Gm::MH;
+    constexpr u32 STAGE_BYTES = 2 * Q * NT * sizeof(T);
     using Rg = Ring<TY>;
     __shared__ u32 s_rows[RY];   // in-plane offsets of the radius-2 rows (wrapped)
     __shared__ u32 s_cols[RX];   // x of the radius-2 columns (wrapped)
+    __shared__ u32 s_tmem;       // TMEM base address of the block
+    __shared__ __align__(8) unsigned long long s_bar;   // TMA completion barrier
 
     const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
     const int idx_in = (ty + 2) * RX + (tx + 2);
+    // staging buffer for the TMA boxes: after the rings, 128-byte aligned
+    const u32 smem_base = smem_addr(lbfe_smem4);
+    const u32 stage_addr = (smem_base + (u32)(sizeof(float) * Gm::FLOATS) + 127u) & ~127u;
+    const T *stage = reinterpret_cast<const T *>(reinterpret_cast<const char *>(lbfe_smem4) + (stage_addr - smem_base));
+    const u32 bar = smem_addr(&s_bar);
+    u32 parity = 0;
+    bool waits_ok = true;
 
-    for (int item = blockIdx.x; item < total_items; item += gridDim.x) {
-        const int k = find_inst(item_off, n_inst, item);
-        const InstDev &I = insts[k];
+    if (ty == 0) tm_alloc(&s_tmem, Gm::TMEM_COLS);
+    if (t == 0) mbar_init(bar);
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    // this warp's TMEM slot: lane quarter ty % 4, columns (ty / 4) * 128
+    const u32 tm_warp = s_tmem + ((u32)(32 * (ty & 3)) << 16) + (u32)((ty >> 2) * 128);
+
+    // the first plane of the block's first item
+    if (t == 0 && blockIdx.x < A.total_items) {
+        const ItemPos P0 = item_pos<TY>(A, blockIdx.x);
+        if (A.inst[P0.k].tma) issue_plane<TY>(A, P0, P0.z0 - 2, stage_addr, bar, STAGE_BYTES);
+    }
+
+    for (int item = blockIdx.x; item < A.total_items; item += gridDim.x) {
+        const ItemPos P = item_pos<TY>(A, item);
+        const int k = P.k;
+        const StepInst &I = A.inst[k];
         const int Lx = I.Lx, Ly = I.Ly, Lz = I.Lz;
-        const int LxLy = Lx * Ly;
-        const u32 S = (u32)I.S;
-        int local = item - __ldg(item_off + k);
-        const int bx = local % I.ntx;
-        local /= I.ntx;
-        const int by = local % I.nty;
-        const int zi = local / I.nty;
-        const int z0 = zi * I.zc, z1 = min(Lz, z0 + I.zc);
+        const int LxLy = I.LxLy;
+        const u32 S = I.S;
+        const int bx = P.bx, by = P.by, z0 = P.z0, z1 = P.z1;
         const int x0 = bx * TX - 2, y0 = by * TY - 2;
-        const T *__restrict__ fin = (const T *)I.f[cur];
-        T *__restrict__ fout = (T *)I.f[cur ^ 1];
-        const float *__restrict__ Cin = I.C[cur];
-        float *__restrict__ Cout = I.C[cur ^ 1];
+        const bool tma = I.tma != 0;
+        const T *__restrict__ fin = (const T *)I.fin;
+        T *__restrict__ fout = (T *)I.fout;
+        const float *__restrict__ Cin = I.Cin;
+        float *__restrict__ Cout = I.Cout;
         const float Uw = I.Uw;
 
         __syncthreads();  // previous item done with the row/column tables
@@ -343,12 +649,15 @@ k_fused(const InstDev *__restrict__ insts, const int *__restrict__ item_off, int
         for (int a = 0; a < 3; ++a)
 #pragma unroll
             for (int b = 0; b < 3; ++b) dxy[a][b] = (int)(s_rows[ty + 1 + b] + s_cols[tx + 1 + a]) - (int)ofs_in;
-        // in-plane offsets of this thread's stage-M cells (i = t + r NT)
-        u32 om_ofs[MR];
+        // in-plane offsets and ring indices of this thread's halo cells
+        u32 h_ofs[MH];
+        int h_idx[MH];
 #pragma unroll
-        for (int r = 0; r < MR; ++r) {
-            const int i = min(t + r * NT, R2N - 1), gy = i / RX;
-            om_ofs[r] = s_rows[gy] + s_cols[i - gy * RX];
+        for (int r = 0; r < MH; ++r) {
+            int gx, gy;
+            ring2_coord<TY>(min(t + r * NT, Gm::NRING2 - 1), gx, gy);
+            h_ofs[r] = s_rows[gy] + s_cols[gx];
+            h_idx[r] = gy * RX + gx;
         }
 
         float FA[3], FB[3], uo[3], rAo = 1.f, rBo = 0.f;
@@ -374,16 +683,40 @@ k_fused(const InstDev *__restrict__ insts, const int *__restrict__ item_off, int
             {
                 const u32 pl = (u32)(min(max(p, 0), Lz - 1) * LxLy);
 #pragma unroll
-                for (int rr = 0; rr < MR; ++rr) {
-                    const int i = t + rr * NT;
-                    if (rr * NT + NT <= R2N || i < R2N) {
+                for (int rr = 0; rr < MH; ++rr) {
+                    if (rr * NT + NT <= Gm::NRING2 || t + rr * NT < Gm::NRING2) {
                         MCell m;
-                        m_load<T>(I, fin, Cin, S, pl + om_ofs[rr], cur, m);
-                        m_store<TY>(I, m, i, L.r3[2], ring2(p), L.cf[2]);
+                        m_load<T>(I, fin, Cin, S, pl + h_ofs[rr], m);
+                        m_store<TY>(I, m, h_idx[rr], L.r3[2], ring2(p), L.cf[2]);
                     }
+                }
+                if (tma) {
+                    waits_ok &= mbar_wait(bar, parity);
+                    parity ^= 1u;
+                }
+                {
+                    // own cell; its populations wait in TMEM for stage X(p)
+                    MCell m;
+                    if (tma && valid)
+                        m_load_staged<T, NT>(I, stage, t, Cin, S, pl + ofs_in, m);
+                    else
+                        m_load<T>(I, fin, Cin, S, pl + ofs_in, m);
+                    m_store<TY>(I, m, idx_in, L.r3[2], ring2(p), L.cf[2]);
+                    tm_store38(tm_warp + (u32)((p & 1) * 64), m.f);
                 }
             }
             __syncthreads();
+            // the staging buffer is free: start the copy of the next plane
+            // (of this item, else of the block's next item)
+            if (t == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                if (p < z1 + 1) {
+                    if (tma) issue_plane<TY>(A, P, p + 1, stage_addr, bar, STAGE_BYTES);
+                } else if (item + (int)gridDim.x < A.total_items) {
+                    const ItemPos Pn = item_pos<TY>(A, item + gridDim.x);
+                    if (A.inst[Pn.k].tma) issue_plane<TY>(A, Pn, Pn.z0 - 2, stage_addr, bar, STAGE_BYTES);
+                }
+            }
             // ---------------- stage F(q): radius-1 region
             if (q >= max(z0 - 1, 0) && q <= min(z1, Lz - 1)) {
                 stage_f_cell<TY>(I, idx_in, L, FA, FB, uo, rAo, rBo);
@@ -396,36 +729,33 @@ k_fused(const InstDev *__restrict__ insts, const int *__restrict__ item_off, int
             }
             // ---------------- stage X(q): collision + push streaming (own cell only:
             // needs no barrier after stage F)
-            if (q >= z0 && q < z1 && valid) {
-                const u32 nq = (u32)(q * LxLy) + ofs_in;
-                const float2 od = offset_dens<T>(I, cur, nq);
+            if (q >= z0 && q < z1) {
                 float fx[2 * Q];
-#pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    fx[i] = ldpop(fin + (long long)i * S + nq, wq(i) * od.x);
-                    fx[Q + i] = ldpop(fin + (long long)(Q + i) * S + nq, wq(i) * od.y);
+                tm_load38(tm_warp + (u32)((q & 1) * 64), fx);   // whole warp
+                if (valid) {
+                    const u32 nq = (u32)(q * LxLy) + ofs_in;
+                    const float rt = rAo + rBo;
+                    if (!(rt > 0.f) || uo[0] != uo[0] || uo[1] != uo[1] || uo[2] != uo[2])
+                        raise_step_flag(A.status, I, kFlagDiverged);
+                    const float nu = (rAo * I.nu_A + rBo * I.nu_B) / rt;
+                    const float om = 1.0f / (3.0f * nu + 0.5f);
+                    const bool bottom = q == 0, top = q == Lz - 1;
+                    PushOffsets Po;
+                    const float2 *rho_s = reinterpret_cast<const float2 *>(smem() + Rg::RHO);
+                    Po.ring[0] = rho_s + L.r3[0] * R2N;
+                    Po.ring[1] = rho_s + L.r3[1] * R2N;
+                    Po.ring[2] = rho_s + L.r3[2] * R2N;
+                    Po.idx = idx_in;
+                    Po.own[0] = rAo;
+                    Po.own[1] = rBo;
+                    Po.track = I.dens_out != nullptr;
+                    Po.r0[0] = I.rho0A;
+                    Po.r0[1] = I.rho0B;
+                    collide_push<T, RX>(fx, fout, S, 0, rAo, Po, uo, FA, om, nq, bottom, top, Uw, LxLy, dxy);
+                    collide_push<T, RX>(fx + Q, fout, S, 1, rBo, Po, uo, FB, om, nq, bottom, top, Uw, LxLy, dxy);
+                    // this step's densities: the offsets of the state just written
+                    if (Store<T>::offset && Po.track) I.dens_out[nq] = make_float2(rAo, rBo);
                 }
-                const float rt = rAo + rBo;
-                if (!(rt > 0.f) || uo[0] != uo[0] || uo[1] != uo[1] || uo[2] != uo[2])
-                    raise_flag(status, I, kFlagDiverged);
-                const float nu = (rAo * I.nu_A + rBo * I.nu_B) / rt;
-                const float om = 1.0f / (3.0f * nu + 0.5f);
-                const bool bottom = q == 0, top = q == Lz - 1;
-                PushOffsets P;
-                const float2 *rho_s = reinterpret_cast<const float2 *>(smem() + Rg::RHO);
-                P.ring[0] = rho_s + L.r3[0] * R2N;
-                P.ring[1] = rho_s + L.r3[1] * R2N;
-                P.ring[2] = rho_s + L.r3[2] * R2N;
-                P.idx = idx_in;
-                P.own[0] = rAo;
-                P.own[1] = rBo;
-                P.track = I.dens[0] != nullptr;
-                P.r0[0] = I.rho0[0];
-                P.r0[1] = I.rho0[1];
-                collide_push<T, true, RX>(fx, fout, S, 0, rAo, P, uo, FA, om, nq, bottom, top, Uw, LxLy, dxy);
-                collide_push<T, true, RX>(fx + Q, fout, S, 1, rBo, P, uo, FB, om, nq, bottom, top, Uw, LxLy, dxy);
-                // this step's densities: the offsets of the state just written
-                if (Store<T>::offset && P.track) I.dens[cur][nq] = make_float2(rAo, rBo);
             }
             __syncthreads();  // u of plane q complete on the radius-1 region
             // ---------------- stage U(r): FENE-P update, Eq. 2 (Eq. 4)
@@ -476,30 +806,148 @@ k_fused(const InstDev *__restrict__ insts, const int *__restrict__ item_off, int
                     const float relax = (fp * c[q6] - (q6 < 3 ? 1.f : 0.f)) * I.inv_tauP;
                     Cout[(u32)(q6 * S + n)] = c[q6] + (-adv[q6] + st - relax);
                 }
-                if (!(c[0] + c[1] + c[2] < I.L2)) raise_flag(status, I, kFlagDiverged);
+                if (!(c[0] + c[1] + c[2] < I.L2)) raise_step_flag(A.status, I, kFlagDiverged);
             }
             __syncthreads();  // stage U done with the rings before stage M(p+1)
         }
     }
+
+    if (!waits_ok) {
+        // a copy may still be in flight: give it one more bounded wait
+        mbar_wait(bar, parity);
+        if (t == 0) atomicOr(A.status, kFlagTimeout);
+    }
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    if (ty == 0) tm_dealloc(s_tmem, Gm::TMEM_COLS);
 }
 
 // ---------------------------------------------------------------- host side
+namespace {
+
+void fill_inst(StepInst &d, const InstDev &I, const PopMaps *maps, int cur) {
+    d = StepInst{};
+    if (maps && maps->ok) {
+        d.pop_map = maps->f[cur];
+        d.tma = 1;
+    }
+    d.Lx = I.Lx;
+    d.Ly = I.Ly;
+    d.Lz = I.Lz;
+    d.LxLy = I.Lx * I.Ly;
+    d.visc_comp = I.visc_comp;
+    d.ntx = I.ntx;
+    d.nty = I.nty;
+    d.zc = I.zc;
+    d.S = (u32)I.S;
+    d.fin = I.f[cur];
+    d.fout = I.f[cur ^ 1];
+    d.Cin = I.C[cur];
+    d.Cout = I.C[cur ^ 1];
+    d.dens_in = I.dens[cur ^ 1];
+    d.dens_out = I.dens[cur];
+    d.status = I.status;
+    d.G = I.G;
+    d.Uw = I.Uw;
+    d.nu_A = I.nu_A;
+    d.nu_B = I.nu_B;
+    d.pi_coef = I.pi_coef;
+    d.L2 = I.L2;
+    d.inv_tauP = I.inv_tauP;
+    d.gx = I.gx;
+    d.gy = I.gy;
+    d.gz = I.gz;
+    d.rho0A = I.rho0[0];
+    d.rho0B = I.rho0[1];
+}
+
+// Dynamic shared memory: rings, alignment slack, TMA staging buffer.
 template <typename T, int TY>
-static cudaError_t fused_t(const LaunchCtx &c, int cur) {
-    const size_t smem = sizeof(float) * Geom<TY>::FLOATS;
-    k_fused<T, TY><<<c.fused_grid, Geom<TY>::NT, smem, c.stream>>>(c.inst_dev, c.item_off, c.n, c.total_items,
-                                                                    cur, c.status);
+constexpr size_t smem_bytes() {
+    return sizeof(float) * Geom<TY>::FLOATS + 128 + sizeof(T) * 2 * Q * Geom<TY>::NT;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// One launch over instances [k0, k1) (at most kStepMaxInst of them).
+template <typename T, int TY>
+cudaError_t fused_group(const LaunchCtx &c, int cur, int k0, int k1) {
+    StepArgs a{};
+    a.n = k1 - k0;
+    a.status = c.status;
+    const int base = c.item_off_host[k0];
+    for (int k = k0; k < k1; ++k) {
+        a.item_off[k - k0] = c.item_off_host[k] - base;
+        fill_inst(a.inst[k - k0], c.inst_host[k], c.maps_host ? c.maps_host + k : nullptr, cur);
+    }
+    a.item_off[a.n] = c.item_off_host[k1] - base;
+    a.total_items = a.item_off[a.n];
+    if (a.total_items <= 0) return cudaSuccess;
+    const int grid = a.total_items < c.fused_slots ? a.total_items : c.fused_slots;
+    const size_t smem = smem_bytes<T, TY>();
+    k_fused<T, TY><<<grid, Geom<TY>::NT, smem, c.stream>>>(a);
     return cudaGetLastError();
 }
 
+template <typename T, int TY>
+cudaError_t fused_t(const LaunchCtx &c, int cur) {
+    for (int k0 = 0; k0 < c.n; k0 += kStepMaxInst) {
+        const int k1 = k0 + kStepMaxInst < c.n ? k0 + kStepMaxInst : c.n;
+        cudaError_t e = fused_group<T, TY>(c, cur, k0, k1);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 template <int TY>
-static cudaError_t fused_ty(const LaunchCtx &c, int cur) {
+cudaError_t fused_ty(const LaunchCtx &c, int cur) {
     switch (c.precision) {
         case LBFE_FP16_OFFSET: return fused_t<__half, TY>(c, cur);
         case LBFE_BF16_OFFSET: return fused_t<__nv_bfloat16, TY>(c, cur);
         default: return fused_t<float, TY>(c, cur);
     }
 }
+
+template <typename T, int TY>
+cudaError_t prep_t(int *bps) {
+    const size_t smem = smem_bytes<T, TY>();
+    cudaError_t e = cudaFuncSetAttribute(k_fused<T, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int b = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fused<T, TY>, Geom<TY>::NT, smem);
+    if (e != cudaSuccess) return e;
+    // resident blocks of one SM share its 512 TMEM columns
+    const int tm = 512 / Geom<TY>::TMEM_COLS;
+    *bps = b < tm ? b : tm;
+    return cudaSuccess;
+}
+
+template <int TY>
+cudaError_t prep_ty(int precision, int *bps) {
+    switch (precision) {
+        case LBFE_FP16_OFFSET: return prep_t<__half, TY>(bps);
+        case LBFE_BF16_OFFSET: return prep_t<__nv_bfloat16, TY>(bps);
+        default: return prep_t<float, TY>(bps);
+    }
+}
+
+}  // namespace
 
 cudaError_t launch_fused(const LaunchCtx &c, int cur) {
     switch (c.tile_y) {
@@ -509,29 +957,36 @@ cudaError_t launch_fused(const LaunchCtx &c, int cur) {
     }
 }
 
-size_t fused_smem_bytes(int tile_y) {
-    switch (tile_y) {
-        case 4: return sizeof(float) * Geom<4>::FLOATS;
-        case 16: return sizeof(float) * Geom<16>::FLOATS;
-        default: return sizeof(float) * Geom<8>::FLOATS;
-    }
-}
+int fused_launches(int n) { return n <= 1 ? 1 : (n + kStepMaxInst - 1) / kStepMaxInst; }
 
-template <typename T, int TY>
-static cudaError_t prep_t(int *bps) {
-    const size_t smem = sizeof(float) * Geom<TY>::FLOATS;
-    cudaError_t e = cudaFuncSetAttribute(k_fused<T, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_fused<T, TY>, Geom<TY>::NT, smem);
-}
-
-template <int TY>
-static cudaError_t prep_ty(int precision, int *bps) {
-    switch (precision) {
-        case LBFE_FP16_OFFSET: return prep_t<__half, TY>(bps);
-        case LBFE_BF16_OFFSET: return prep_t<__nv_bfloat16, TY>(bps);
-        default: return prep_t<float, TY>(bps);
+// The populations of an instance viewed as a 4-D tensor (x, y, z, s*19 + i)
+// with strides (1, Lx, Lx Ly, S) elements; the box is one tile-plane of all
+// 38 populations.  TMA needs every stride to be a multiple of 16 bytes, so
+// instances with Lx * element size not divisible by 16 keep ordinary loads.
+cudaError_t fused_pop_maps(const InstDev &I, int precision, int tile_y, PopMaps *m) {
+    std::memset(m, 0, sizeof *m);
+    const size_t esz = precision == LBFE_FP32 ? 4 : 2;
+    if (((size_t)I.Lx * esz) % 16 != 0) return cudaSuccess;
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return cudaSuccess;
+    const CUtensorMapDataType dt = precision == LBFE_FP16_OFFSET   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                   : precision == LBFE_BF16_OFFSET ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                                   : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const cuuint64_t dims[4] = {(cuuint64_t)I.Lx, (cuuint64_t)I.Ly, (cuuint64_t)I.Lz, (cuuint64_t)(2 * Q)};
+    const cuuint64_t strides[3] = {(cuuint64_t)I.Lx * esz, (cuuint64_t)I.Lx * I.Ly * esz, (cuuint64_t)I.S * esz};
+    const cuuint32_t box[4] = {32u, (cuuint32_t)tile_y, 1u, (cuuint32_t)(2 * Q)};
+    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+    for (int b = 0; b < 2; ++b) {
+        const CUresult r = fn(&m->f[b], dt, 4, I.f[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            std::memset(m, 0, sizeof *m);
+            return cudaSuccess;
+        }
     }
+    m->ok = 1;
+    return cudaSuccess;
 }
 
 cudaError_t fused_prepare(int tile_y, int precision, int *blocks_per_sm) {

@@ -3,6 +3,7 @@
 // populations, the per-instance descriptor and the step launchers.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -125,6 +126,7 @@ __device__ __forceinline__ float peterlin(float L2, float cxx, float cyy, float 
 
 // Status bits written by the kernels into the handle's status word.
 constexpr unsigned kFlagDiverged = 1u;
+constexpr unsigned kFlagTimeout = 2u;    // a bounded device-side wait expired (launch status only)
 
 // Launchers (lbfe_fused.cu, lbfe_fields.cu, lbfe_obs.cu).
 struct LaunchCtx {
@@ -135,11 +137,23 @@ struct LaunchCtx {
     unsigned *status;                // device status word
     cudaStream_t stream;
     const int *item_off;             // device [n+1]: first fused work item of each instance
+    const int *item_off_host;        // host copy of item_off
     int total_items, fused_grid, tile_y;
+    int fused_slots;                 // resident blocks of the fused kernel on the GPU
+    const struct PopMaps *maps_host; // per instance: TMA maps of the step kernel (may be null)
 };
+// Tensor maps of the step kernel's own-tile TMA loads, one per population
+// buffer f[0], f[1] of an instance; ok = 0 when the instance's layout does
+// not allow them (the kernel then reads those cells with ordinary loads).
+struct PopMaps {
+    CUtensorMap f[2];
+    int ok;
+};
+cudaError_t fused_pop_maps(const InstDev &I, int precision, int tile_y, PopMaps *m);
 cudaError_t launch_fused(const LaunchCtx &c, int cur);
-// Shared memory and resident blocks per SM of the fused kernel for a tile height.
-size_t fused_smem_bytes(int tile_y);
+// Kernel launches of one time step of n instances.
+int fused_launches(int n);
+// Resident blocks per SM of the fused kernel for a tile height.
 cudaError_t fused_prepare(int tile_y, int precision, int *blocks_per_sm);
 cudaError_t launch_moments(const LaunchCtx &c, int cur);
 cudaError_t launch_forces(const LaunchCtx &c, int cur);
