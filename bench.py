@@ -232,7 +232,7 @@ def run_ours(a):
     with torch.cuda.stream(stream):
         s = lbfe.Solver(ps, device=f"cuda:{local}", stream=stream)
         if shape:
-            s.tune(shape["tile_y"], shape["z_chunk"])
+            s.tune(shape["tile_y"], shape["z_chunk"], shape.get("kernel", 0))
         for k, r in enumerate(rhos):
             s.init(k, r)
         for _ in range(a.warmup):
@@ -271,7 +271,7 @@ def run_ours(a):
         with torch.cuda.stream(stream):
             s2 = lbfe.Solver(ps, device=f"cuda:{local}", stream=stream)
             if shape:
-                s2.tune(shape["tile_y"], shape["z_chunk"])
+                s2.tune(shape["tile_y"], shape["z_chunk"], shape.get("kernel", 0))
             for k, hbuf in enumerate(hosts):
                 s2.init_from_host_ptr(k, hbuf.data_ptr())
             s2.step(2)

@@ -172,18 +172,28 @@ lbfe_status lbfe_get_field(lbfe_handle *h, int k, int which, void *host_dst, siz
 lbfe_status lbfe_set_field(lbfe_handle *h, int k, int which, const void *host_src, size_t bytes);
 
 /* Number of kernel launches one lbfe_step(h, 1) enqueues: one per group of
- * up to 64 instances (the step kernel carries the instance descriptors in
+ * up to 56 instances (the step kernel carries the instance descriptors in
  * its parameter space). */
 int lbfe_launches_per_step(const lbfe_handle *h);
 
-/* Launch shape of the step kernel: column-tile height tile_y in {4, 8, 16}
- * (tile width 32) and z-chunk depth in planes (0 = automatic: fill the
- * resident blocks of the GPU about once).  Affects speed only; results are
- * identical for every shape.  Synchronises the stream. */
-lbfe_status lbfe_tune(lbfe_handle *h, int tile_y, int z_chunk);
-/* Current launch shape (any output may be NULL): tile height, z-chunk of
- * instance 0, persistent grid size and number of work items. */
-lbfe_status lbfe_launch_config(const lbfe_handle *h, int *tile_y, int *z_chunk, int *grid, int *items);
+/* Variants of the time-step kernel.  Both compute the same step (results
+ * agree to FP32 rounding); they differ in speed only. */
+typedef enum {
+    LBFE_STEP_CELL = 0,   /* one cell per thread, tiles of 32 x tile_y cells, tile_y in {8, 12, 16} */
+    LBFE_STEP_PAIR = 1    /* two x-adjacent cells per thread, 32 x 16 tiles; needs even Lx everywhere */
+} lbfe_step_kernel;
+
+/* Launch shape of the step kernel: variant (lbfe_step_kernel), column-tile
+ * height tile_y (tile width 32; 16 for LBFE_STEP_PAIR) and z-chunk depth in
+ * planes (0 = automatic: fill the resident blocks of the GPU about once).
+ * LBFE_ERR_BAD_PARAM for an unsupported combination.  Synchronises the
+ * stream. */
+lbfe_status lbfe_tune(lbfe_handle *h, int step_kernel, int tile_y, int z_chunk);
+/* Current launch shape (any output may be NULL): kernel variant, tile
+ * height, z-chunk of instance 0, persistent grid size and number of work
+ * items. */
+lbfe_status lbfe_launch_config(const lbfe_handle *h, int *step_kernel, int *tile_y, int *z_chunk, int *grid,
+                               int *items);
 
 /* Observables of a population field the caller already holds on the
  * device, computed without allocating anything.  For callers that cannot

@@ -215,7 +215,8 @@ struct lbfe_handle {
     int *item_off = nullptr;
     std::vector<int> item_off_h;
     std::vector<lbfe::PopMaps> maps;
-    int total_items = 0, fused_grid = 0, tile_y = 8, z_chunk_req = 0, num_sms = 0, blocks_per_sm = 0;
+    int total_items = 0, fused_grid = 0, tile_y = 16, z_chunk_req = 0, num_sms = 0, blocks_per_sm = 0;
+    int step_kernel = LBFE_STEP_CELL;
     unsigned *status = nullptr;
     double *mass = nullptr;
     int cur = 0;
@@ -237,6 +238,7 @@ struct lbfe_handle {
         c.total_items = total_items;
         c.fused_grid = fused_grid;
         c.tile_y = tile_y;
+        c.step_kernel = step_kernel;
         return c;
     }
 };
@@ -245,11 +247,17 @@ struct lbfe_handle {
 // column tiles times nzc z-chunks.  Without a requested chunk depth, nzc is
 // chosen so that the items fill the resident blocks of the GPU about once
 // (chunks of at least 8 planes).
-static lbfe_status configure_fused(lbfe_handle *h, int tile_y, int z_chunk) {
-    if (tile_y != 4 && tile_y != 8 && tile_y != 16) return LBFE_ERR_BAD_PARAM;
+static lbfe_status configure_fused(lbfe_handle *h, int step_kernel, int tile_y, int z_chunk) {
+    if (step_kernel == LBFE_STEP_PAIR) {
+        if (tile_y != 16) return LBFE_ERR_BAD_PARAM;
+        for (auto &I : h->inst)
+            if (I.Lx % 2) return LBFE_ERR_BAD_PARAM;
+    } else if (step_kernel != LBFE_STEP_CELL || (tile_y != 8 && tile_y != 12 && tile_y != 16)) {
+        return LBFE_ERR_BAD_PARAM;
+    }
     if (z_chunk < 0) return LBFE_ERR_BAD_PARAM;
     int bps = 0;
-    cudaError_t e = lbfe::fused_prepare(tile_y, h->precision, &bps);
+    cudaError_t e = lbfe::fused_prepare(step_kernel, tile_y, h->precision, &bps);
     if (e != cudaSuccess) return cuda_fail(e, "fused_prepare");
     if (bps < 1) return LBFE_ERR_BAD_PARAM;
     long long columns = 0;
@@ -277,6 +285,7 @@ static lbfe_status configure_fused(lbfe_handle *h, int tile_y, int z_chunk) {
         off[k + 1] = off[k] + (int)items;
     }
     h->tile_y = tile_y;
+    h->step_kernel = step_kernel;
     h->z_chunk_req = z_chunk;
     h->blocks_per_sm = bps;
     h->total_items = off[h->n];
@@ -425,7 +434,7 @@ lbfe_status lbfe_create(lbfe_handle **hp, const lbfe_params *p, int n, void *dev
         delete h;
         return cuda_fail(e, "lbfe_create");
     }
-    lbfe_status st = configure_fused(h, 8, 0);
+    lbfe_status st = configure_fused(h, LBFE_STEP_CELL, 16, 0);
     if (st != LBFE_OK) {
         delete h;
         return st;
@@ -637,13 +646,15 @@ lbfe_status lbfe_set_field(lbfe_handle *h, int k, int which, const void *host_sr
 
 int lbfe_launches_per_step(const lbfe_handle *h) { return h ? lbfe::fused_launches(h->n) : 0; }
 
-lbfe_status lbfe_tune(lbfe_handle *h, int tile_y, int z_chunk) {
+lbfe_status lbfe_tune(lbfe_handle *h, int step_kernel, int tile_y, int z_chunk) {
     if (!h) return LBFE_ERR_BAD_PARAM;
-    return configure_fused(h, tile_y, z_chunk);
+    return configure_fused(h, step_kernel, tile_y, z_chunk);
 }
 
-lbfe_status lbfe_launch_config(const lbfe_handle *h, int *tile_y, int *z_chunk, int *grid, int *items) {
+lbfe_status lbfe_launch_config(const lbfe_handle *h, int *step_kernel, int *tile_y, int *z_chunk, int *grid,
+                               int *items) {
     if (!h) return LBFE_ERR_BAD_PARAM;
+    if (step_kernel) *step_kernel = h->step_kernel;
     if (tile_y) *tile_y = h->tile_y;
     if (z_chunk) *z_chunk = h->inst[0].zc;
     if (grid) *grid = h->fused_grid;

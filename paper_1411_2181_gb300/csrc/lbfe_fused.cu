@@ -1,594 +1,20 @@
-// lbfe_fused.cu -- one time step of the hybrid LBM / FENE-P method (Sec. 2)
-// in a single persistent kernel that reads every population and conformation
-// component once and writes it once.
-//
-// Work decomposition.  A work item is a column tile of 32 x TY cells in the
-// x-y plane over a chunk [z0, z1) of planes of one instance; blocks stride
-// over the work items of all instances of a batch.  Inside an item the block
-// marches along z with shared-memory rings holding, per plane, the fields the
-// stencils need:
-//   stage M(p)    moments rho_A, rho_B, j and the polymer stress
-//                 Pi = (eta_P/tau_P) chi (f C - I) of plane p on the
-//                 radius-2 region (36 x (TY+4) cells; the halo is recomputed
-//                 from the populations of the neighbouring columns);
-//   stage F(p-1)  Shan-Chen force (radius-1 densities), polymer force
-//                 div Pi, the Guo velocity u = (j + F/2)/rho on the radius-1
-//                 region (34 x (TY+2));
-//   stage X(p-1)  BGK + Guo collision of the tile's own cells and push
-//                 streaming with halfway bounce-back on the moving walls;
-//   stage U(p-2)  FENE-P update of C (Eq. 2/4): central grad u from the
-//                 velocity ring, first-order upwind u.grad C from the
-//                 conformation ring.
-// The collision of plane p-1 needs the densities of plane p (Shan-Chen); the
-// C update of plane p-2 needs the velocity of plane p-1, hence the lags.
-// Three block barriers per plane: after stage M, after stage X (stage X
-// needs only its own cell's forces, so it runs before the barrier that
-// stage U needs) and after stage U.
-// Planes beyond a wall are loaded as the adjacent plane (mirror ghosts of
-// rho, C and Pi); the velocity ghost 2 U_wall - u is applied in stage U.
-//
-// Blackwell specifics.
-//  * The tile's own 32 x TY populations of the next plane arrive by one TMA
-//    tensor copy (box 32 x TY x 1 x 38 of the (x, y, z, population) view)
-//    into a shared-memory staging buffer, issued as soon as stage M has
-//    consumed the buffer: the DRAM reads of plane p+1 overlap stages F, X
-//    and U of plane p.  Completion is tracked by an mbarrier with a bounded
-//    wait.  The radius-2 halo (recomputed) and ragged-tile cells are read
-//    with ordinary loads.
-//  * Each thread's own-cell populations, decoded to FP32 in stage M(p), wait
-//    in tensor memory (TMEM) for the collision X(p) one plane later: two
-//    plane buffers of 38 columns per warp in the warp's 32-lane quarter,
-//    written and read with tcgen05.st / tcgen05.ld.  The collision therefore
-//    issues no global loads, and the register file does not hold the
-//    populations across the stencil stages.
-//  * The instance descriptors travel in the kernel parameter space (up to
-//    64 instances per launch): scalars and pointers come from the constant
-//    bank instead of per-use global loads.
+// lbfe_fused.cu -- the time-step kernel with one cell per thread (tiles of
+// 32 x TY cells, TY in {8, 12, 16}), and the host side of both step kernels:
+// launch descriptors, TMA tensor maps and the grouping of a batch into
+// launches.  The stage structure is described in lbfe_step.cuh.
 #include <cstring>
 #include <mutex>
 
-#include "lbfe_internal.cuh"
+#include "lbfe_step.cuh"
 
 namespace lbfe {
 
-namespace {
-
-typedef unsigned int u32;
-
-template <int TY>
-struct Geom {
-    static constexpr int TX = 32;
-    static constexpr int NT = TX * TY;                 // threads = tile cells
-    static constexpr int WARPS = NT / 32;
-    static constexpr int RX = TX + 4, RY = TY + 4;     // radius-2 region
-    static constexpr int R2N = RX * RY;
-    static constexpr int NRING1 = 2 * (RX - 2) + 2 * TY;  // radius-1 cells outside the tile
-    static constexpr int NRING2 = 4 * TX + 4 * RY;        // radius-2 region cells outside the tile
-    static constexpr int MH = (NRING2 + NT - 1) / NT;     // stage-M halo rounds per thread
-    // rings: rho (float2) x3, stress scalars (a f, a) x3, j 3x2, C 6x4, u 3x3
-    static constexpr int FLOATS = (2 * 3 + 2 * 3 + 6 + 24 + 9) * R2N;
-    // TMEM: per warp two plane buffers in 64-column slots; warps w, w+4, ...
-    // share the lane quarter w % 4 and take consecutive 128-column ranges
-    static constexpr int TMEM_COLS = (WARPS / 4) * 128;
-    static_assert(WARPS % 4 == 0 && TMEM_COLS >= 32 && TMEM_COLS <= 512, "TMEM layout");
-};
-
-// ---------------------------------------------------------------- descriptors
-constexpr int kStepMaxInst = 64;
-
-// Per-instance descriptor of one launch (kernel parameter space).
-struct StepInst {
-    CUtensorMap pop_map;           // (x, y, z, population) view of fin, box 32 x TY x 1 x 38 (when tma)
-    int tma;                       // own-tile populations by TMA
-    int Lx, Ly, Lz, LxLy;
-    int visc_comp, ntx, nty, zc;   // visc_comp: 0 (A), 1 (B), -1 Newtonian
-    u32 S, pad_;                   // field stride
-    const void *fin;               // populations read (state t)
-    void *fout;                    // populations written (state t + 1)
-    const float *Cin;
-    float *Cout;
-    const float2 *dens_in;         // offsets of the state read (reduced forms with tracking, else null)
-    float2 *dens_out;              // offsets of the state written
-    unsigned *status;              // per-instance status word (may be null)
-    float G, Uw, nu_A, nu_B, pi_coef, L2, inv_tauP, gx, gy, gz, rho0A, rho0B;
-};
-
-// One launch covers up to kStepMaxInst instances.  A single instance takes
-// the same kernel as a batch, so that batching never changes the arithmetic
-// (the results of an instance are bitwise the same alone or in a batch).
-struct StepArgs {
-    int n, total_items;
-    unsigned *status;              // status word of the launch
-    int item_off[kStepMaxInst + 1];  // first work item of each instance
-    StepInst inst[kStepMaxInst];
-};
-
-__device__ __forceinline__ void raise_step_flag(unsigned *global, const StepInst &I, unsigned flag) {
-    atomicOr(global, flag);
-    if (I.status) atomicOr(I.status, flag);
-}
-
-// ---------------------------------------------------------------- TMEM access
-__device__ __forceinline__ u32 smem_addr(const void *p) { return (u32)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void tm_alloc(u32 *dst, u32 ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst)),
-                 "r"(ncols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tm_dealloc(u32 taddr, u32 ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tm_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
-// ---------------------------------------------------------------- TMA + mbarrier
-constexpr int kWaitLimit = 1 << 22;   // try_wait rounds before a wait is declared expired
-
-__device__ __forceinline__ void mbar_init(u32 bar) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-// One thread: arm the barrier for `bytes` and start the copy of the box at
-// (x, y, z, 0) into shared memory at dst.
-__device__ __forceinline__ void tma_pop_box(const CUtensorMap *map, u32 dst, u32 bar, u32 bytes, int x, int y, int z) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
-        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(0), "r"(bar)
-        : "memory");
-}
-// Wait for the completion of phase `parity`; false once the limit expired.
-__device__ __forceinline__ bool mbar_wait(u32 bar, u32 parity) {
-    for (int it = 0; it < kWaitLimit; ++it) {
-        u32 ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tm_st32(u32 taddr, const float *v) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};"
-                 :: "r"(taddr),
-                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
-                 "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
-                 "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
-                 "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])),
-                 "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])), "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])),
-                 "r"(__float_as_uint(v[20])), "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
-                 "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])), "r"(__float_as_uint(v[27])),
-                 "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])), "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
-                 );
-}
-__device__ __forceinline__ void tm_st4(u32 taddr, const float *v) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};"
-                 :: "r"(taddr),
-                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3]))
-                 );
-}
-__device__ __forceinline__ void tm_st2(u32 taddr, const float *v) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};"
-                 :: "r"(taddr),
-                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1]))
-                 );
-}
-__device__ __forceinline__ void tm_ld32(u32 taddr, u32 *r) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-                 : 
-                   "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-                   "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-                   "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                 : "r"(taddr));
-}
-__device__ __forceinline__ void tm_ld4(u32 taddr, u32 *r) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(taddr));
-}
-__device__ __forceinline__ void tm_ld2(u32 taddr, u32 *r) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
-                 : "=r"(r[0]), "=r"(r[1])
-                 : "r"(taddr));
-}
-// Completes the loads above; the registers pass through the statement so
-// that no use of them can be scheduled before the wait.
-__device__ __forceinline__ void tm_wait_ld38(u32 *r) {
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 :
-                 "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
-                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]),
-                 "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
-                 "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]),
-                 "+r"(r[32]), "+r"(r[33]), "+r"(r[34]), "+r"(r[35]), "+r"(r[36]), "+r"(r[37])
-                 );
-}
-
-// The 38 populations of a cell: columns [0, 38) of a plane buffer.
-__device__ __forceinline__ void tm_store38(u32 taddr, const float *v) {
-    tm_st32(taddr, v);
-    tm_st4(taddr + 32, v + 32);
-    tm_st2(taddr + 36, v + 36);
-}
-__device__ __forceinline__ void tm_load38(u32 taddr, float *v) {
-    u32 r[38];
-    tm_wait_st();
-    tm_ld32(taddr, r);
-    tm_ld4(taddr + 32, r + 32);
-    tm_ld2(taddr + 36, r + 36);
-    tm_wait_ld38(r);
-#pragma unroll
-    for (int i = 0; i < 38; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// ---------------------------------------------------------------- rings
-// Ring slot of plane p (p >= -4) in rings of 2, 3 and 4 planes.
-__device__ __forceinline__ int ring2(int p) { return (p + 12) & 1; }
-__device__ __forceinline__ int ring3(int p) { return (p + 12) % 3; }
-__device__ __forceinline__ int ring4(int p) { return (p + 12) & 3; }
-__device__ __forceinline__ int wrapg(int a, int L) { a %= L; return a < 0 ? a + L : a; }
-
-// symmetric-tensor slot of (a, b): xx, yy, zz, xy, xz, yz
-__host__ __device__ constexpr int symk(int a, int b) {
-    return a == b ? a : ((a + b) == 1 ? 3 : ((a + b) == 2 ? 4 : 5));
-}
-
-template <typename T>
-__device__ __forceinline__ float ldpop(const T *p, float add) {
-    float v = Store<T>::ld(p);
-    if (Store<T>::offset) v += add;
-    return v;
-}
-
-// Cell h (0 <= h < NRING1) of the radius-1 region outside the tile.
-template <int TY>
-__device__ __forceinline__ void ring1_coord(int h, int &gx, int &gy) {
-    using Gm = Geom<TY>;
-    if (h < 2 * (Gm::RX - 2)) {
-        const int rr = h / (Gm::RX - 2);
-        gx = 1 + (h - rr * (Gm::RX - 2));
-        gy = rr == 0 ? 1 : Gm::RY - 2;
-    } else {
-        const int h2 = h - 2 * (Gm::RX - 2);
-        const int cc = h2 / TY;
-        gy = 2 + (h2 - cc * TY);
-        gx = cc == 0 ? 1 : Gm::RX - 2;
-    }
-}
-
-// Cell h (0 <= h < NRING2) of the radius-2 region outside the tile: first
-// the four halo rows over the tile's own 32 columns (one aligned row per
-// warp), then the two-column strips left and right of the tile, row by row.
-template <int TY>
-__device__ __forceinline__ void ring2_coord(int h, int &gx, int &gy) {
-    if (h < 128) {
-        const int r = h >> 5;
-        gy = r < 2 ? r : TY + r;   // rows 0, 1, TY + 2, TY + 3
-        gx = 2 + (h & 31);
-    } else {
-        const int j = h - 128;
-        gy = j >> 2;               // 0 .. TY + 3
-        const int c = j & 3;
-        gx = c < 2 ? c : 32 + c;   // columns 0, 1, 34, 35
-    }
-}
-
-// Shared-memory rings (offsets in floats from the dynamic shared base):
-//   rho  float2 [3][R2N]          densities rho_A, rho_B
-//   pi   float  [3][2][R2N]       a f and a of Pi = a (f C) - a I, a = (eta_P/tau_P) chi
-//   j    float  [2][3][R2N]       momentum
-//   c    float  [4][6][R2N]       conformation
-//   u    float  [3][3][R2N]       velocity
-template <int TY>
-struct Ring {
-    static constexpr int R2N = Geom<TY>::R2N;
-    static constexpr int RHO = 0, PI = 6 * R2N, J = PI + 6 * R2N, C = J + 6 * R2N, U = C + 24 * R2N;
-};
-
-extern __shared__ float4 lbfe_smem4[];
-__device__ __forceinline__ float *smem() { return reinterpret_cast<float *>(lbfe_smem4); }
-
-// Stage M inputs of one cell: its 38 populations (decoded to FP32) and 6
-// conformation components.
-struct MCell {
-    float f[2 * Q];
-    float c[6];
-};
-
-// Cell offsets are 32-bit: an instance holds at most 2^26 cells, so every
-// field offset (s*19 + i)*S + n stays below 2^32.
-template <typename T>
-__device__ __forceinline__ void m_load(const StepInst &I, const T *__restrict__ fin, const float *__restrict__ Cin,
-                                       u32 S, u32 n, MCell &m) {
-    float ra0 = 0.f, rb0 = 0.f;
-    if (Store<T>::offset) {
-        if (I.dens_in) {
-            const float2 od = __ldg(I.dens_in + n);
-            ra0 = od.x;
-            rb0 = od.y;
-        } else {
-            ra0 = I.rho0A;
-            rb0 = I.rho0B;
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        m.f[i] = ldpop(fin + (u32)(i * S + n), wq(i) * ra0);
-        m.f[Q + i] = ldpop(fin + (u32)((Q + i) * S + n), wq(i) * rb0);
-    }
-#pragma unroll
-    for (int k = 0; k < 6; ++k) m.c[k] = __ldg(Cin + (u32)(k * S + n));
-}
-
-// As m_load, with the populations taken from the TMA staging buffer
-// (element (x, y, i) of the box at i * NT + y * 32 + x).
-template <typename T, int NT>
-__device__ __forceinline__ void m_load_staged(const StepInst &I, const T *stage, int t,
-                                              const float *__restrict__ Cin, u32 S, u32 n, MCell &m) {
-    float ra0 = 0.f, rb0 = 0.f;
-    if (Store<T>::offset) {
-        if (I.dens_in) {
-            const float2 od = __ldg(I.dens_in + n);
-            ra0 = od.x;
-            rb0 = od.y;
-        } else {
-            ra0 = I.rho0A;
-            rb0 = I.rho0B;
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        m.f[i] = Store<T>::ld_plain(stage + i * NT + t);
-        m.f[Q + i] = Store<T>::ld_plain(stage + (Q + i) * NT + t);
-        if (Store<T>::offset) {
-            m.f[i] += wq(i) * ra0;
-            m.f[Q + i] += wq(i) * rb0;
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 6; ++k) m.c[k] = __ldg(Cin + (u32)(k * S + n));
-}
-
-// Stage M for one cell: moments, stress scalars and conformation into the
-// ring slots of its plane.
-template <int TY>
-__device__ __forceinline__ void m_store(const StepInst &I, const MCell &m, int idx, int s3, int s2, int s4) {
-    // s3: rho / stress slot, s2: j slot, s4: C slot of the plane
-    constexpr int R2N = Geom<TY>::R2N;
-    using Rg = Ring<TY>;
-    float2 *rho_s = reinterpret_cast<float2 *>(smem() + Rg::RHO) + s3 * R2N;
-    float *pi_s = smem() + Rg::PI + s3 * 2 * R2N;
-    float *j_s = smem() + Rg::J + s2 * 3 * R2N;
-    float *c_s = smem() + Rg::C + s4 * 6 * R2N;
-    float rA = 0.f, rB = 0.f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) { rA += m.f[i]; rB += m.f[Q + i]; }
-    // momentum from opposite-pair differences (exact in FP32 per pair)
-    float jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-    for (int i = 1; i < Q; i += 2) {
-        const float d = (m.f[i] - m.f[i + 1]) + (m.f[Q + i] - m.f[Q + i + 1]);
-        if (cx(i)) jx += cx(i) * d;
-        if (cy(i)) jy += cy(i) * d;
-        if (cz(i)) jz += cz(i) * d;
-    }
-    rho_s[idx] = make_float2(rA, rB);
-    j_s[idx] = jx;
-    j_s[R2N + idx] = jy;
-    j_s[2 * R2N + idx] = jz;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) c_s[k * R2N + idx] = m.c[k];
-    float a = 0.f, fp = 1.f;
-    if (I.visc_comp >= 0) {
-        a = I.pi_coef * (I.visc_comp == 0 ? rA : rB) / (rA + rB);
-        fp = peterlin(I.L2, m.c[0], m.c[1], m.c[2]);
-    }
-    pi_s[idx] = a * fp;
-    pi_s[R2N + idx] = a;
-}
-
-// Ring slots of the planes one iteration touches (q = p - 1, r = p - 2).
-struct Slots {
-    int r3[3];   // rho / stress / u slots of planes q-1, q, q+1
-    int ur[3];   // u slots of planes r-1, r, r+1 (= q-2, q-1, q)
-    int cf[3];   // C slots of planes q-1, q, q+1 (stage F)
-    int cu[3];   // C slots of planes r-1, r, r+1 (stage U)
-    int j3;      // j slot of plane q (ring of 2)
-};
-
-// Stage F for one cell of plane q: Shan-Chen and polymer forces and the
-// velocity.  Writes u to the ring; returns the per-component total forces,
-// u and the densities.
-template <int TY>
-__device__ __forceinline__ void stage_f_cell(const StepInst &I, int idx, const Slots &L, float FA[3], float FB[3],
-                                             float u[3], float &rA, float &rB) {
-    constexpr int R2N = Geom<TY>::R2N, RX = Geom<TY>::RX;
-    using Rg = Ring<TY>;
-    const float2 *rho0 = reinterpret_cast<const float2 *>(smem() + Rg::RHO);
-    const float2 *rm = rho0 + L.r3[0] * R2N, *rc = rho0 + L.r3[1] * R2N, *rp = rho0 + L.r3[2] * R2N;
-    const float2 r0 = rc[idx];
-    rA = r0.x;
-    rB = r0.y;
-    // Shan-Chen with opposite neighbours in pairs: w_i c_i (rho(x + c_i) - rho(x - c_i))
-    float sA[3] = {0.f, 0.f, 0.f}, sB[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int i = 1; i < Q; i += 2) {
-        const int o = cx(i) + cy(i) * RX;
-        const float2 a = (cz(i) > 0 ? rp : (cz(i) < 0 ? rm : rc))[idx + o];
-        const float2 b = (cz(i) > 0 ? rm : (cz(i) < 0 ? rp : rc))[idx - o];
-        const float dA = a.x - b.x, dB = a.y - b.y, w = wq(i);
-        if (cx(i)) { sA[0] += cx(i) * w * dB; sB[0] += cx(i) * w * dA; }
-        if (cy(i)) { sA[1] += cy(i) * w * dB; sB[1] += cy(i) * w * dA; }
-        if (cz(i)) { sA[2] += cz(i) * w * dB; sB[2] += cz(i) * w * dA; }
-    }
-    // polymer force F_P,a = sum_b (Pi_ba(x + e_b) - Pi_ba(x - e_b))/2 with
-    // Pi_ba = (a f) C_ba - a delta_ba
-    float FP[3] = {0.f, 0.f, 0.f};
-    if (I.visc_comp >= 0) {
-        const float *sm_ = smem() + Rg::PI + L.r3[0] * 2 * R2N;
-        const float *sc_ = smem() + Rg::PI + L.r3[1] * 2 * R2N;
-        const float *sp_ = smem() + Rg::PI + L.r3[2] * 2 * R2N;
-        const float *cm = smem() + Rg::C + L.cf[0] * 6 * R2N;
-        const float *cc = smem() + Rg::C + L.cf[1] * 6 * R2N;
-        const float *cp = smem() + Rg::C + L.cf[2] * 6 * R2N;
-        const float afxp = sc_[idx + 1], afxm = sc_[idx - 1], afyp = sc_[idx + RX], afym = sc_[idx - RX];
-        const float afzp = sp_[idx], afzm = sm_[idx];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            float gxd = afxp * cc[symk(0, a) * R2N + idx + 1] - afxm * cc[symk(0, a) * R2N + idx - 1];
-            float gyd = afyp * cc[symk(1, a) * R2N + idx + RX] - afym * cc[symk(1, a) * R2N + idx - RX];
-            float gzd = afzp * cp[symk(2, a) * R2N + idx] - afzm * cm[symk(2, a) * R2N + idx];
-            if (a == 0) gxd -= sc_[R2N + idx + 1] - sc_[R2N + idx - 1];
-            if (a == 1) gyd -= sc_[R2N + idx + RX] - sc_[R2N + idx - RX];
-            if (a == 2) gzd -= sp_[R2N + idx] - sm_[R2N + idx];
-            FP[a] = 0.5f * (gxd + gyd + gzd);
-        }
-    }
-    const float g[3] = {I.gx, I.gy, I.gz};
-    const float inv = 1.0f / (rA + rB);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        FA[a] = -I.G * rA * sA[a] + (rA * inv) * FP[a] + rA * g[a];
-        FB[a] = -I.G * rB * sB[a] + (rB * inv) * FP[a] + rB * g[a];
-        u[a] = (smem()[Rg::J + L.j3 * 3 * R2N + a * R2N + idx] + 0.5f * (FA[a] + FB[a])) * inv;
-        smem()[Rg::U + L.r3[1] * 3 * R2N + a * R2N + idx] = u[a];
-    }
-}
-
-// Offsets of the reduced storage forms at the destination of a push:
-// the destination cell's densities of this step (from the density ring of
-// planes q-1, q, q+1), or the constant offsets when densities are not
-// tracked.
-struct PushOffsets {
-    const float2 *ring[3];   // density ring slots of planes q-1, q, q+1
-    int idx;                 // ring index of the pushing cell
-    float own[2];            // the pushing cell's densities
-    bool track;
-    float r0[2];             // constant offsets
-};
-
-template <int RX>
-__device__ __forceinline__ float push_offset(const PushOffsets &P, int s, int d, bool wall) {
-    if (!P.track) return P.r0[s];
-    if (wall) return P.own[s];
-    const float2 v = P.ring[cz(d) + 1][P.idx + cx(d) + cy(d) * RX];
-    return s == 0 ? v.x : v.y;
-}
-
-// Store post-collision population d of the cell at offset n into its
-// streamed position x + c_d.  A population whose target lies beyond a wall returns into the cell as the opposite direction (halfway
-// bounce-back) with the moving-wall term -6 w_d rho_s (c_d . U_wall).
-template <typename T, int RX>
-__device__ __forceinline__ void push_one(T *__restrict__ fdst, u32 S, int s, int d, float v, float rs,
-                                         const PushOffsets &P, u32 n, bool bottom, bool top, float Uw, int LxLy,
-                                         const int dxy[3][3]) {
-    int dir = d;
-    u32 dst = n + (u32)(cz(d) * LxLy + dxy[cx(d) + 1][cy(d) + 1]);
-    bool wall = false;
-    if ((cz(d) < 0 && bottom) || (cz(d) > 0 && top)) {
-        v -= 6.f * wq(d) * rs * (float)cx(d) * (cz(d) < 0 ? -Uw : Uw);
-        dir = opp(d);
-        dst = n;
-        wall = true;
-    }
-    if (Store<T>::offset) v -= wq(d) * push_offset<RX>(P, s, d, wall);
-    Store<T>::st(fdst + (u32)((s * Q + dir) * S + dst), v);
-}
-
-// BGK + Guo collision of one component at one cell and push streaming of
-// its 19 populations.  Opposite directions share the symmetric parts:
-//   f^eq_{i,-i} = w rho (1 + 9/2 (c.u)^2 - 3/2 u.u) +- 3 w rho (c.u)
-//   S_{i,-i}    = (1 - 1/2tau) w (9 (c.u)(c.F) - 3 u.F) +- 3 (1 - 1/2tau) w (c.F)
-// so that with E = omega rho (1 - 3/2 u.u) - 3 (1 - 1/2tau) u.F the
-// post-collision pair is (1 - omega) f_{i,-i} + sym +- anti,
-//   sym  = w E + (c.u) (9/2 omega rho w (c.u) + 9 (1 - 1/2tau) w (c.F)),
-//   anti = 3 omega rho w (c.u) + 3 (1 - 1/2tau) w (c.F),
-// with the weight products formed once per weight class.
-template <typename T, int RX>
-__device__ __forceinline__ void collide_push(const float *fv, T *__restrict__ fdst, u32 S, int s, float rs,
-                                             const PushOffsets &P, const float u[3], const float F[3], float om, u32 n,
-                                             bool bottom, bool top, float Uw, int LxLy, const int dxy[3][3]) {
-    const float omc = 1.0f - om, pref = 1.0f - 0.5f * om;
-    const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    const float uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
-    const float E = om * (rs * (1.f - 1.5f * uu)) - 3.f * pref * uF;
-    const float a1 = 4.5f * om * rs, b1 = 9.f * pref, a2 = 3.f * om * rs, b2 = 3.f * pref;
-    {
-        float v = omc * fv[0] + wq(0) * E;
-        if (Store<T>::offset) v -= wq(0) * (P.track ? P.own[s] : P.r0[s]);
-        Store<T>::st(fdst + (u32)(s * Q * S + n), v);
-    }
-    // weight classes: faces (i = 1..6) and edges (i = 7..18)
-    float Ew[2], a1w[2], b1w[2], a2w[2], b2w[2];
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        const float w = wq(c == 0 ? 1 : 7);
-        Ew[c] = w * E;
-        a1w[c] = w * a1;
-        b1w[c] = w * b1;
-        a2w[c] = w * a2;
-        b2w[c] = w * b2;
-    }
-#pragma unroll
-    for (int i = 1; i < Q; i += 2) {
-        const int c = i <= 6 ? 0 : 1;
-        const float cu = cx(i) * u[0] + cy(i) * u[1] + cz(i) * u[2];
-        const float cF = cx(i) * F[0] + cy(i) * F[1] + cz(i) * F[2];
-        const float sym = fmaf(cu, fmaf(a1w[c], cu, b1w[c] * cF), Ew[c]);
-        const float anti = fmaf(a2w[c], cu, b2w[c] * cF);
-        push_one<T, RX>(fdst, S, s, i, fmaf(omc, fv[i], sym + anti), rs, P, n, bottom, top, Uw, LxLy, dxy);
-        push_one<T, RX>(fdst, S, s, i + 1, fmaf(omc, fv[i + 1], sym - anti), rs, P, n, bottom, top, Uw,
-                               LxLy, dxy);
-    }
-}
-
-}  // namespace
-
-// Position of work item `item`: instance, column tile and z-chunk.
-struct ItemPos {
-    int k, bx, by, z0, z1;
-};
-
-template <int TY>
-__device__ __forceinline__ ItemPos item_pos(const StepArgs &A, int item) {
-    ItemPos P;
-    P.k = 0;
-    for (int hi = A.n - 1; P.k < hi;) {
-        const int mid = (P.k + hi + 1) >> 1;
-        if (A.item_off[mid] <= item) P.k = mid; else hi = mid - 1;
-    }
-    const StepInst &I = A.inst[P.k];
-    int local = item - A.item_off[P.k];
-    P.bx = local % I.ntx;
-    local /= I.ntx;
-    P.by = local % I.nty;
-    P.z0 = (local / I.nty) * I.zc;
-    P.z1 = min(I.Lz, P.z0 + I.zc);
-    return P;
-}
-
-template <int TY>
-__device__ __forceinline__ void issue_plane(const StepArgs &A, const ItemPos &P, int plane, u32 dst, u32 bar,
-                                            u32 bytes) {
-    const StepInst &I = A.inst[P.k];
-    tma_pop_box(&I.pop_map, dst, bar, bytes, P.bx * 32, P.by * TY, min(max(plane, 0), I.Lz - 1));
-}
-
 template <typename T, int TY>
-__global__ void __launch_bounds__(32 * TY, TY >= 16 ? 1 : (TY >= 8 ? 2 : 3))
+__global__ void __launch_bounds__(32 * TY, 1)
 k_fused(const __grid_constant__ StepArgs A) {
     using Gm = Geom<TY>;
     constexpr int TX = Gm::TX, NT = Gm::NT, RX = Gm::RX, RY = Gm::RY, R2N = Gm::R2N, MH = Gm::MH;
-    constexpr u32 STAGE_BYTES = 2 * Q * NT * sizeof(T);
+    using St = Stage<T, TY>;
     using Rg = Ring<TY>;
     __shared__ u32 s_rows[RY];   // in-plane offsets of the radius-2 rows (wrapped)
     __shared__ u32 s_cols[RX];   // x of the radius-2 columns (wrapped)
@@ -601,6 +27,7 @@ k_fused(const __grid_constant__ StepArgs A) {
     const u32 smem_base = smem_addr(lbfe_smem4);
     const u32 stage_addr = (smem_base + (u32)(sizeof(float) * Gm::FLOATS) + 127u) & ~127u;
     const T *stage = reinterpret_cast<const T *>(reinterpret_cast<const char *>(lbfe_smem4) + (stage_addr - smem_base));
+    const float *stage_c = reinterpret_cast<const float *>(reinterpret_cast<const char *>(stage) + St::C_OFF);
     const u32 bar = smem_addr(&s_bar);
     u32 parity = 0;
     bool waits_ok = true;
@@ -616,7 +43,7 @@ k_fused(const __grid_constant__ StepArgs A) {
     // the first plane of the block's first item
     if (t == 0 && blockIdx.x < A.total_items) {
         const ItemPos P0 = item_pos<TY>(A, blockIdx.x);
-        if (A.inst[P0.k].tma) issue_plane<TY>(A, P0, P0.z0 - 2, stage_addr, bar, STAGE_BYTES);
+        if (A.inst[P0.k].tma) issue_plane<T, TY>(A, P0, P0.z0 - 2, stage_addr, bar);
     }
 
     for (int item = blockIdx.x; item < A.total_items; item += gridDim.x) {
@@ -649,15 +76,23 @@ k_fused(const __grid_constant__ StepArgs A) {
         for (int a = 0; a < 3; ++a)
 #pragma unroll
             for (int b = 0; b < 3; ++b) dxy[a][b] = (int)(s_rows[ty + 1 + b] + s_cols[tx + 1 + a]) - (int)ofs_in;
-        // in-plane offsets and ring indices of this thread's halo cells
+        // this thread's halo cells: in-plane offsets, ring indices, region
+        // coordinates and whether they lie inside the domain (inside the
+        // region copy) rather than across a periodic seam
         u32 h_ofs[MH];
-        int h_idx[MH];
+        int h_idx[MH], h_gx[MH], h_gy[MH];
+        bool h_on[MH], h_dom[MH];
 #pragma unroll
         for (int r = 0; r < MH; ++r) {
             int gx, gy;
             ring2_coord<TY>(min(t + r * NT, Gm::NRING2 - 1), gx, gy);
+            h_on[r] = (r + 1) * NT <= Gm::NRING2 || t + r * NT < Gm::NRING2;
             h_ofs[r] = s_rows[gy] + s_cols[gx];
             h_idx[r] = gy * RX + gx;
+            h_gx[r] = gx;
+            h_gy[r] = gy;
+            const int xg = x0 + gx, yg = y0 + gy;
+            h_dom[r] = xg >= 0 && xg < Lx && yg >= 0 && yg < Ly;
         }
 
         float FA[3], FB[3], uo[3], rAo = 1.f, rBo = 0.f;
@@ -682,13 +117,20 @@ k_fused(const __grid_constant__ StepArgs A) {
             // ---------------- stage M(p): radius-2 region of plane clamp(p)
             {
                 const u32 pl = (u32)(min(max(p, 0), Lz - 1) * LxLy);
+                MCell mh[MH];
+                if (St::REGION) {
+                    // halo cells across the periodic seams (not in the copied
+                    // box) load first; their latency overlaps the staged work
 #pragma unroll
-                for (int rr = 0; rr < MH; ++rr) {
-                    if (rr * NT + NT <= Gm::NRING2 || t + rr * NT < Gm::NRING2) {
-                        MCell m;
-                        m_load<T>(I, fin, Cin, S, pl + h_ofs[rr], m);
-                        m_store<TY>(I, m, h_idx[rr], L.r3[2], ring2(p), L.cf[2]);
-                    }
+                    for (int rr = 0; rr < MH; ++rr)
+                        if (h_on[rr] && !(tma && h_dom[rr])) m_load<T>(I, fin, Cin, S, pl + h_ofs[rr], mh[rr]);
+                } else {
+#pragma unroll
+                    for (int rr = 0; rr < MH; ++rr)
+                        if (h_on[rr]) {
+                            m_load<T>(I, fin, Cin, S, pl + h_ofs[rr], mh[rr]);
+                            m_store<TY>(I, mh[rr], h_idx[rr], L.r3[2], ring2(p), L.cf[2]);
+                        }
                 }
                 if (tma) {
                     waits_ok &= mbar_wait(bar, parity);
@@ -697,12 +139,25 @@ k_fused(const __grid_constant__ StepArgs A) {
                 {
                     // own cell; its populations wait in TMEM for stage X(p)
                     MCell m;
-                    if (tma && valid)
-                        m_load_staged<T, NT>(I, stage, t, Cin, S, pl + ofs_in, m);
-                    else
+                    if (tma && valid) {
+                        if (St::REGION)
+                            m_load_region<T, TY>(I, stage, stage_c, tx + 2, ty + 2, pl + ofs_in, m);
+                        else
+                            m_load_staged<T, NT>(I, stage, t, Cin, S, pl + ofs_in, m);
+                    } else {
                         m_load<T>(I, fin, Cin, S, pl + ofs_in, m);
+                    }
                     m_store<TY>(I, m, idx_in, L.r3[2], ring2(p), L.cf[2]);
                     tm_store38(tm_warp + (u32)((p & 1) * 64), m.f);
+                }
+                if (St::REGION) {
+#pragma unroll
+                    for (int rr = 0; rr < MH; ++rr)
+                        if (h_on[rr]) {
+                            if (tma && h_dom[rr])
+                                m_load_region<T, TY>(I, stage, stage_c, h_gx[rr], h_gy[rr], pl + h_ofs[rr], mh[rr]);
+                            m_store<TY>(I, mh[rr], h_idx[rr], L.r3[2], ring2(p), L.cf[2]);
+                        }
                 }
             }
             __syncthreads();
@@ -711,10 +166,10 @@ k_fused(const __grid_constant__ StepArgs A) {
             if (t == 0) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 if (p < z1 + 1) {
-                    if (tma) issue_plane<TY>(A, P, p + 1, stage_addr, bar, STAGE_BYTES);
+                    if (tma) issue_plane<T, TY>(A, P, p + 1, stage_addr, bar);
                 } else if (item + (int)gridDim.x < A.total_items) {
                     const ItemPos Pn = item_pos<TY>(A, item + gridDim.x);
-                    if (A.inst[Pn.k].tma) issue_plane<TY>(A, Pn, Pn.z0 - 2, stage_addr, bar, STAGE_BYTES);
+                    if (A.inst[Pn.k].tma) issue_plane<T, TY>(A, Pn, Pn.z0 - 2, stage_addr, bar);
                 }
             }
             // ---------------- stage F(q): radius-1 region
@@ -760,53 +215,11 @@ k_fused(const __grid_constant__ StepArgs A) {
             __syncthreads();  // u of plane q complete on the radius-1 region
             // ---------------- stage U(r): FENE-P update, Eq. 2 (Eq. 4)
             if (r >= z0 && r < z1 && valid) {
-                const float *um = smem() + Rg::U + L.ur[0] * 3 * R2N;
-                const float *uc = smem() + Rg::U + L.ur[1] * 3 * R2N;
-                const float *up = smem() + Rg::U + L.ur[2] * 3 * R2N;
-                const float *cm = smem() + Rg::C + L.cu[0] * 6 * R2N;
-                const float *cc = smem() + Rg::C + L.cu[1] * 6 * R2N;
-                const float *cp = smem() + Rg::C + L.cu[2] * 6 * R2N;
-                const int i0 = idx_in;
-                float u0[3], Gr[3][3];
-#pragma unroll
-                for (int j = 0; j < 3; ++j) u0[j] = uc[j * R2N + i0];
-                // grad u by central differences, u_ghost = 2 U_wall - u at the walls
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    const float uwb = j == 0 ? -Uw : 0.f, uwt = j == 0 ? Uw : 0.f;
-                    const float uzp = (r == Lz - 1) ? 2.f * uwt - u0[j] : up[j * R2N + i0];
-                    const float uzm = (r == 0) ? 2.f * uwb - u0[j] : um[j * R2N + i0];
-                    Gr[0][j] = 0.5f * (uc[j * R2N + i0 + 1] - uc[j * R2N + i0 - 1]);
-                    Gr[1][j] = 0.5f * (uc[j * R2N + i0 + RX] - uc[j * R2N + i0 - RX]);
-                    Gr[2][j] = 0.5f * (uzp - uzm);
-                }
-                float c[6];
-#pragma unroll
-                for (int q6 = 0; q6 < 6; ++q6) c[q6] = cc[q6 * R2N + i0];
-                // first-order upwind u . grad C (C mirrored at the walls)
-                const int ox = u0[0] > 0.f ? -1 : 1, oy = u0[1] > 0.f ? -RX : RX;
-                const float sx = u0[0] > 0.f ? u0[0] : -u0[0], sy = u0[1] > 0.f ? u0[1] : -u0[1];
-                const float sz = u0[2] > 0.f ? u0[2] : -u0[2];
-                const float *cz_ = u0[2] > 0.f ? cm : cp;
-                float adv[6];
-#pragma unroll
-                for (int q6 = 0; q6 < 6; ++q6)
-                    adv[q6] = sx * (c[q6] - cc[q6 * R2N + i0 + ox]) + sy * (c[q6] - cc[q6 * R2N + i0 + oy]) +
-                              sz * (c[q6] - cz_[q6 * R2N + i0]);
-                const float Cm[3][3] = {{c[0], c[3], c[4]}, {c[3], c[1], c[5]}, {c[4], c[5], c[2]}};
-                const float fp = peterlin(I.L2, c[0], c[1], c[2]);
+                float cn[6];
+                if (!stage_u_cell<TY>(I, idx_in, L, r, cn)) raise_step_flag(A.status, I, kFlagDiverged);
                 const u32 n = (u32)(r * LxLy) + ofs_in;
 #pragma unroll
-                for (int q6 = 0; q6 < 6; ++q6) {
-                    const int a = q6 < 3 ? q6 : (q6 == 5 ? 1 : 0);
-                    const int b = q6 < 3 ? q6 : (q6 == 3 ? 1 : 2);
-                    float st = 0.f;
-#pragma unroll
-                    for (int m = 0; m < 3; ++m) st += Cm[a][m] * Gr[m][b] + Gr[m][a] * Cm[m][b];
-                    const float relax = (fp * c[q6] - (q6 < 3 ? 1.f : 0.f)) * I.inv_tauP;
-                    Cout[(u32)(q6 * S + n)] = c[q6] + (-adv[q6] + st - relax);
-                }
-                if (!(c[0] + c[1] + c[2] < I.L2)) raise_step_flag(A.status, I, kFlagDiverged);
+                for (int q6 = 0; q6 < 6; ++q6) Cout[(u32)(q6 * S + n)] = cn[q6];
             }
             __syncthreads();  // stage U done with the rings before stage M(p+1)
         }
@@ -830,6 +243,7 @@ void fill_inst(StepInst &d, const InstDev &I, const PopMaps *maps, int cur) {
     d = StepInst{};
     if (maps && maps->ok) {
         d.pop_map = maps->f[cur];
+        d.c_map = maps->c[cur];
         d.tma = 1;
     }
     d.Lx = I.Lx;
@@ -865,7 +279,7 @@ void fill_inst(StepInst &d, const InstDev &I, const PopMaps *maps, int cur) {
 // Dynamic shared memory: rings, alignment slack, TMA staging buffer.
 template <typename T, int TY>
 constexpr size_t smem_bytes() {
-    return sizeof(float) * Geom<TY>::FLOATS + 128 + sizeof(T) * 2 * Q * Geom<TY>::NT;
+    return sizeof(float) * Geom<TY>::FLOATS + 128 + Stage<T, TY>::BYTES;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -886,42 +300,18 @@ EncodeTiledFn encode_tiled() {
     return fn;
 }
 
-// One launch over instances [k0, k1) (at most kStepMaxInst of them).
 template <typename T, int TY>
-cudaError_t fused_group(const LaunchCtx &c, int cur, int k0, int k1) {
-    StepArgs a{};
-    a.n = k1 - k0;
-    a.status = c.status;
-    const int base = c.item_off_host[k0];
-    for (int k = k0; k < k1; ++k) {
-        a.item_off[k - k0] = c.item_off_host[k] - base;
-        fill_inst(a.inst[k - k0], c.inst_host[k], c.maps_host ? c.maps_host + k : nullptr, cur);
-    }
-    a.item_off[a.n] = c.item_off_host[k1] - base;
-    a.total_items = a.item_off[a.n];
-    if (a.total_items <= 0) return cudaSuccess;
-    const int grid = a.total_items < c.fused_slots ? a.total_items : c.fused_slots;
-    const size_t smem = smem_bytes<T, TY>();
-    k_fused<T, TY><<<grid, Geom<TY>::NT, smem, c.stream>>>(a);
+cudaError_t cell_launch_t(const StepArgs &a, int grid, cudaStream_t st) {
+    k_fused<T, TY><<<grid, Geom<TY>::NT, smem_bytes<T, TY>(), st>>>(a);
     return cudaGetLastError();
 }
 
-template <typename T, int TY>
-cudaError_t fused_t(const LaunchCtx &c, int cur) {
-    for (int k0 = 0; k0 < c.n; k0 += kStepMaxInst) {
-        const int k1 = k0 + kStepMaxInst < c.n ? k0 + kStepMaxInst : c.n;
-        cudaError_t e = fused_group<T, TY>(c, cur, k0, k1);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-}
-
 template <int TY>
-cudaError_t fused_ty(const LaunchCtx &c, int cur) {
-    switch (c.precision) {
-        case LBFE_FP16_OFFSET: return fused_t<__half, TY>(c, cur);
-        case LBFE_BF16_OFFSET: return fused_t<__nv_bfloat16, TY>(c, cur);
-        default: return fused_t<float, TY>(c, cur);
+cudaError_t cell_launch_ty(const StepArgs &a, int grid, int precision, cudaStream_t st) {
+    switch (precision) {
+        case LBFE_FP16_OFFSET: return cell_launch_t<__half, TY>(a, grid, st);
+        case LBFE_BF16_OFFSET: return cell_launch_t<__nv_bfloat16, TY>(a, grid, st);
+        default: return cell_launch_t<float, TY>(a, grid, st);
     }
 }
 
@@ -947,39 +337,86 @@ cudaError_t prep_ty(int precision, int *bps) {
     }
 }
 
+// One launch over instances [k0, k1) (at most kStepMaxInst of them).
+cudaError_t fused_group(const LaunchCtx &c, int cur, int k0, int k1) {
+    StepArgs a{};
+    a.n = k1 - k0;
+    a.status = c.status;
+    const int base = c.item_off_host[k0];
+    for (int k = k0; k < k1; ++k) {
+        a.item_off[k - k0] = c.item_off_host[k] - base;
+        fill_inst(a.inst[k - k0], c.inst_host[k], c.maps_host ? c.maps_host + k : nullptr, cur);
+    }
+    a.item_off[a.n] = c.item_off_host[k1] - base;
+    a.total_items = a.item_off[a.n];
+    if (a.total_items <= 0) return cudaSuccess;
+    const int grid = a.total_items < c.fused_slots ? a.total_items : c.fused_slots;
+    if (c.step_kernel == LBFE_STEP_PAIR) return step_pair_launch(a, grid, c.precision, c.stream);
+    return step_cell_launch(a, grid, c.tile_y, c.precision, c.stream);
+}
+
 }  // namespace
 
-cudaError_t launch_fused(const LaunchCtx &c, int cur) {
-    switch (c.tile_y) {
-        case 4: return fused_ty<4>(c, cur);
-        case 16: return fused_ty<16>(c, cur);
-        default: return fused_ty<8>(c, cur);
+cudaError_t step_cell_launch(const StepArgs &a, int grid, int tile_y, int precision, cudaStream_t st) {
+    switch (tile_y) {
+        case 12: return cell_launch_ty<12>(a, grid, precision, st);
+        case 16: return cell_launch_ty<16>(a, grid, precision, st);
+        default: return cell_launch_ty<8>(a, grid, precision, st);
     }
+}
+
+cudaError_t step_cell_prepare(int tile_y, int precision, int *blocks_per_sm) {
+    switch (tile_y) {
+        case 12: return prep_ty<12>(precision, blocks_per_sm);
+        case 16: return prep_ty<16>(precision, blocks_per_sm);
+        default: return prep_ty<8>(precision, blocks_per_sm);
+    }
+}
+
+cudaError_t launch_fused(const LaunchCtx &c, int cur) {
+    for (int k0 = 0; k0 < c.n; k0 += kStepMaxInst) {
+        const int k1 = k0 + kStepMaxInst < c.n ? k0 + kStepMaxInst : c.n;
+        cudaError_t e = fused_group(c, cur, k0, k1);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 int fused_launches(int n) { return n <= 1 ? 1 : (n + kStepMaxInst - 1) / kStepMaxInst; }
 
 // The populations of an instance viewed as a 4-D tensor (x, y, z, s*19 + i)
-// with strides (1, Lx, Lx Ly, S) elements; the box is one tile-plane of all
-// 38 populations.  TMA needs every stride to be a multiple of 16 bytes, so
-// instances with Lx * element size not divisible by 16 keep ordinary loads.
+// with strides (1, Lx, Lx Ly, S) elements, and the conformation as
+// (x, y, z, component).  Tiles of 16 rows copy their own 32 x 16 cells;
+// lower tiles copy the radius-2 region (boxes as in Stage).  TMA needs
+// every stride to be a multiple of 16 bytes, so instances with
+// Lx * element size not divisible by 16 keep ordinary loads.
 cudaError_t fused_pop_maps(const InstDev &I, int precision, int tile_y, PopMaps *m) {
     std::memset(m, 0, sizeof *m);
     const size_t esz = precision == LBFE_FP32 ? 4 : 2;
-    if (((size_t)I.Lx * esz) % 16 != 0) return cudaSuccess;
+    if (((size_t)I.Lx * esz) % 16 != 0 || ((size_t)I.Lx * 4) % 16 != 0) return cudaSuccess;
     EncodeTiledFn fn = encode_tiled();
     if (!fn) return cudaSuccess;
     const CUtensorMapDataType dt = precision == LBFE_FP16_OFFSET   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                    : precision == LBFE_BF16_OFFSET ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                                    : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const bool region = tile_y <= 12;
+    const cuuint32_t xpad = (cuuint32_t)(16 / esz);
     const cuuint64_t dims[4] = {(cuuint64_t)I.Lx, (cuuint64_t)I.Ly, (cuuint64_t)I.Lz, (cuuint64_t)(2 * Q)};
     const cuuint64_t strides[3] = {(cuuint64_t)I.Lx * esz, (cuuint64_t)I.Lx * I.Ly * esz, (cuuint64_t)I.S * esz};
-    const cuuint32_t box[4] = {32u, (cuuint32_t)tile_y, 1u, (cuuint32_t)(2 * Q)};
+    const cuuint32_t box[4] = {region ? 32u + 2 * xpad : 32u, (cuuint32_t)(region ? tile_y + 4 : tile_y), 1u,
+                               (cuuint32_t)(2 * Q)};
+    const cuuint64_t cdims[4] = {(cuuint64_t)I.Lx, (cuuint64_t)I.Ly, (cuuint64_t)I.Lz, 6};
+    const cuuint64_t cstrides[3] = {(cuuint64_t)I.Lx * 4, (cuuint64_t)I.Lx * I.Ly * 4, (cuuint64_t)I.S * 4};
+    const cuuint32_t cbox[4] = {40u, (cuuint32_t)(tile_y + 4), 1u, 6u};
     const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
     for (int b = 0; b < 2; ++b) {
-        const CUresult r = fn(&m->f[b], dt, 4, I.f[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        CUresult r = fn(&m->f[b], dt, 4, I.f[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r == CUDA_SUCCESS && region)
+            r = fn(&m->c[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, I.C[b], cdims, cstrides, cbox, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
             std::memset(m, 0, sizeof *m);
             return cudaSuccess;
@@ -989,12 +426,9 @@ cudaError_t fused_pop_maps(const InstDev &I, int precision, int tile_y, PopMaps 
     return cudaSuccess;
 }
 
-cudaError_t fused_prepare(int tile_y, int precision, int *blocks_per_sm) {
-    switch (tile_y) {
-        case 4: return prep_ty<4>(precision, blocks_per_sm);
-        case 16: return prep_ty<16>(precision, blocks_per_sm);
-        default: return prep_ty<8>(precision, blocks_per_sm);
-    }
+cudaError_t fused_prepare(int step_kernel, int tile_y, int precision, int *blocks_per_sm) {
+    if (step_kernel == LBFE_STEP_PAIR) return step_pair_prepare(precision, blocks_per_sm);
+    return step_cell_prepare(tile_y, precision, blocks_per_sm);
 }
 
 }  // namespace lbfe

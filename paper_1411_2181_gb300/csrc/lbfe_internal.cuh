@@ -139,6 +139,7 @@ struct LaunchCtx {
     const int *item_off;             // device [n+1]: first fused work item of each instance
     const int *item_off_host;        // host copy of item_off
     int total_items, fused_grid, tile_y;
+    int step_kernel;                 // lbfe_step_kernel
     int fused_slots;                 // resident blocks of the fused kernel on the GPU
     const struct PopMaps *maps_host; // per instance: TMA maps of the step kernel (may be null)
 };
@@ -146,7 +147,8 @@ struct LaunchCtx {
 // buffer f[0], f[1] of an instance; ok = 0 when the instance's layout does
 // not allow them (the kernel then reads those cells with ordinary loads).
 struct PopMaps {
-    CUtensorMap f[2];
+    CUtensorMap f[2];   // populations f[0], f[1]
+    CUtensorMap c[2];   // conformation C[0], C[1] (region copies)
     int ok;
 };
 cudaError_t fused_pop_maps(const InstDev &I, int precision, int tile_y, PopMaps *m);
@@ -154,7 +156,7 @@ cudaError_t launch_fused(const LaunchCtx &c, int cur);
 // Kernel launches of one time step of n instances.
 int fused_launches(int n);
 // Resident blocks per SM of the fused kernel for a tile height.
-cudaError_t fused_prepare(int tile_y, int precision, int *blocks_per_sm);
+cudaError_t fused_prepare(int step_kernel, int tile_y, int precision, int *blocks_per_sm);
 cudaError_t launch_moments(const LaunchCtx &c, int cur);
 cudaError_t launch_forces(const LaunchCtx &c, int cur);
 cudaError_t launch_init(const LaunchCtx &c, int k, const double *rho_dev, int cur);

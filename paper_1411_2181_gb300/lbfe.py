@@ -24,6 +24,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ct.CDLL(LIB_PATH)
 
 FIELD_F, FIELD_C, FIELD_RHO, FIELD_U = 0, 1, 2, 3
+STEP_CELL, STEP_PAIR = 0, 1   # lbfe_step_kernel
 
 OK, ERR_BAD_PARAM, ERR_NO_MEMORY, ERR_CUDA, ERR_DIVERGED, ERR_TIMEOUT, ERR_STATE = range(7)
 
@@ -69,9 +70,9 @@ _lib.lbfe_set_field.argtypes = [_H, ct.c_int, ct.c_int, ct.c_void_p, ct.c_size_t
 _lib.lbfe_destroy.argtypes = [_H]
 _lib.lbfe_launches_per_step.argtypes = [_H]
 _lib.lbfe_launches_per_step.restype = ct.c_int
-_lib.lbfe_tune.argtypes = [_H, ct.c_int, ct.c_int]
+_lib.lbfe_tune.argtypes = [_H, ct.c_int, ct.c_int, ct.c_int]
 _lib.lbfe_tune.restype = ct.c_int
-_lib.lbfe_launch_config.argtypes = [_H] + [ct.POINTER(ct.c_int)] * 4
+_lib.lbfe_launch_config.argtypes = [_H] + [ct.POINTER(ct.c_int)] * 5
 _lib.lbfe_launch_config.restype = ct.c_int
 _lib.lbfe_observables_noalloc.argtypes = [_P, ct.c_void_p, ct.c_longlong, ct.POINTER(CObs), ct.c_void_p]
 _lib.lbfe_observables_noalloc.restype = ct.c_int
@@ -191,13 +192,15 @@ class Solver:
     def launches_per_step(self) -> int:
         return _lib.lbfe_launches_per_step(self._h)
 
-    def tune(self, tile_y: int = 8, z_chunk: int = 0):
-        _check(_lib.lbfe_tune(self._h, int(tile_y), int(z_chunk)), "lbfe_tune")
+    def tune(self, tile_y: int = 16, z_chunk: int = 0, kernel: int = 0):
+        """Launch shape of the step: kernel STEP_CELL (tile_y in 4, 8, 16) or
+        STEP_PAIR (tile_y 16, even Lx), and the z-chunk depth (0 = auto)."""
+        _check(_lib.lbfe_tune(self._h, int(kernel), int(tile_y), int(z_chunk)), "lbfe_tune")
 
     def launch_config(self) -> dict:
-        v = [ct.c_int() for _ in range(4)]
+        v = [ct.c_int() for _ in range(5)]
         _check(_lib.lbfe_launch_config(self._h, *[ct.byref(x) for x in v]), "lbfe_launch_config")
-        return dict(tile_y=v[0].value, z_chunk=v[1].value, grid=v[2].value, items=v[3].value)
+        return dict(kernel=v[0].value, tile_y=v[1].value, z_chunk=v[2].value, grid=v[3].value, items=v[4].value)
 
     def check(self) -> int:
         return _lib.lbfe_check(self._h)

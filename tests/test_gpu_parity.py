@@ -22,9 +22,16 @@ def L():
     return lbfe
 
 
-def run_pair(L, p, rho=None, steps=1, f0=None, C0=None):
+# step kernel variants (kernel, tile_y): one cell per thread with own-tile
+# staging (16 rows) or region staging (8 rows), two cells per thread
+KERNELS = [(0, 16), (0, 8), (1, 16)]
+
+
+def run_pair(L, p, rho=None, steps=1, f0=None, C0=None, kernel=None):
     """Advance the GPU and the oracle from the same state; return both."""
     s = L.Solver(p)
+    if kernel is not None:
+        s.tune(kernel[1], 0, kernel[0])
     orc = O.Oracle(p.oracle_dict())
     if rho is None:
         rho = np.ones((2, p.Lz, p.Ly, p.Lx))
@@ -44,11 +51,12 @@ def run_pair(L, p, rho=None, steps=1, f0=None, C0=None):
     return s, orc
 
 
-def test_config1_parity_500_steps(L):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_config1_parity_500_steps(L, kernel):
     """32^3, DV, De = 1, 500 steps: populations and conformation within 1e-5
-    (normalised) of the FP64 oracle."""
+    (normalised) of the FP64 oracle, for every step-kernel variant."""
     p, rho, steps = configs.config1()
-    s, orc = run_pair(L, p, rho, steps)
+    s, orc = run_pair(L, p, rho, steps, kernel=kernel)
     C = s.get_field(0, L.FIELD_C)
     ef = norm_err(s.get_field(0, L.FIELD_F), orc.f, 2)
     eC = tensor_err(C, orc.C)
@@ -57,16 +65,21 @@ def test_config1_parity_500_steps(L):
     assert s.check() == L.OK
 
 
-@pytest.mark.parametrize("shape", [(7, 5, 6), (13, 9, 4), (33, 17, 11), (64, 3, 2)])
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("shape", [(7, 5, 6), (13, 9, 4), (33, 17, 11), (64, 3, 2), (66, 19, 7), (2, 1, 2),
+                                   (36, 10, 5)])
 @pytest.mark.parametrize("phase", [0, 1, 2])
-def test_random_state_few_steps_ragged(L, shape, phase):
+def test_random_state_few_steps_ragged(L, shape, phase, kernel):
     """Arbitrary non-equilibrium populations and conformation on boxes whose
-    sizes do not divide the thread blocks; moving walls; every phase."""
+    sizes do not divide the thread blocks; moving walls; every phase; both
+    step kernels (the two-cell kernel on even Lx)."""
     Lx, Ly, Lz = shape
+    if kernel[0] == 1 and Lx % 2:
+        pytest.skip("the two-cell kernel needs even Lx")
     p = L.Params(Lx=Lx, Ly=Ly, Lz=Lz, R=2.0, Uw=0.03, G=3.1, eta_M=0.4, lambda_=1.3, eta_P=0.15,
                  tau_P=6.0, L2=40.0, visco_phase=phase, g=(1e-4, -3e-5, 2e-5))
     f0, C0 = random_populations(shape, seed=sum(shape) + phase)
-    s, orc = run_pair(L, p, None, 1, f0, C0)
+    s, orc = run_pair(L, p, None, 1, f0, C0, kernel=kernel)
     assert norm_err(s.get_field(0, L.FIELD_F), orc.f, 2) < TOL_FEW
     assert tensor_err(s.get_field(0, L.FIELD_C), orc.C) < TOL_FEW
     s.step(4)
@@ -88,13 +101,14 @@ def test_velocity_and_density_fields(L):
     assert norm_err(s.get_field(0, L.FIELD_U), d["u"], 1) < 1e-5
 
 
-def test_full_size_config2_parity(L):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_full_size_config2_parity(L, kernel):
     """Full 192 x 96 x 80 lattice of the matrix-viscoelastic workload, in the
-    benchmark's launch configuration: every cell after 3 steps from a
-    perturbed state."""
+    launch configurations of the benchmark (every step-kernel variant): every
+    cell after 3 steps from a perturbed state."""
     p, rho, _ = configs.config2(0.2)
     f0, C0 = random_populations((p.Lx, p.Ly, p.Lz), seed=21, amp=0.01)
-    s, orc = run_pair(L, p, rho, 3, f0, C0)
+    s, orc = run_pair(L, p, rho, 3, f0, C0, kernel=kernel)
     assert norm_err(s.get_field(0, L.FIELD_F), orc.f, 2) < TOL_FEW
     assert tensor_err(s.get_field(0, L.FIELD_C), orc.C) < TOL_FEW
 
@@ -159,8 +173,9 @@ def test_divergence_is_flagged_not_faulted(L):
         s.observables(0)
 
 
-@pytest.mark.parametrize("tile_y,z_chunk", [(4, 0), (8, 8), (16, 0), (8, 5), (16, 3), (4, 13)])
-def test_launch_shapes_agree(L, tile_y, z_chunk):
+@pytest.mark.parametrize("kernel,tile_y,z_chunk", [(0, 12, 0), (0, 8, 8), (0, 16, 0), (0, 8, 5), (0, 16, 3),
+                                                   (0, 12, 13), (1, 16, 0), (1, 16, 5), (1, 16, 1)])
+def test_launch_shapes_agree(L, kernel, tile_y, z_chunk):
     """Every tile height and z-chunk depth of the fused step gives the same
     fields (ragged box: 40 x 20 x 13 does not divide the 32 x TY tiles)."""
     shape = (40, 20, 13)
@@ -172,9 +187,9 @@ def test_launch_shapes_agree(L, tile_y, z_chunk):
     s.init(0, np.ones((2, 13, 20, 40)))
     s.set_field(0, L.FIELD_F, f0)
     s.set_field(0, L.FIELD_C, C0)
-    s.tune(tile_y, z_chunk)
+    s.tune(tile_y, z_chunk, kernel)
     cfg = s.launch_config()
-    assert cfg["tile_y"] == tile_y
+    assert cfg["tile_y"] == tile_y and cfg["kernel"] == kernel
     s.step(3)
     fg, Cg = s.get_field(0, L.FIELD_F), s.get_field(0, L.FIELD_C)
     assert np.abs(fg - ref.get_field(0, L.FIELD_F)).max() <= 1e-6
@@ -182,9 +197,10 @@ def test_launch_shapes_agree(L, tile_y, z_chunk):
     assert norm_err(fg, orc.f, 2) < TOL_FEW and tensor_err(Cg, orc.C) < TOL_FEW
 
 
-def test_batch_equals_solo_runs(L):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_batch_equals_solo_runs(L, kernel):
     """Instances of uneven size and parameters advanced in one persistent
-    launch give exactly their single-instance results."""
+    launch give exactly their single-instance results (either kernel)."""
     ps = [L.Params(Lx=40, Ly=24, Lz=12, R=4.0, Uw=0.02, G=3.1, eta_M=0.6, eta_P=0.24, tau_P=30.0,
                    visco_phase=1, sigma=0.0592),
           L.Params(Lx=64, Ly=32, Lz=20, R=6.0, Uw=0.03, G=3.1, eta_M=0.9, eta_P=0.36, tau_P=50.0,
@@ -192,11 +208,13 @@ def test_batch_equals_solo_runs(L):
           L.Params(Lx=24, Ly=16, Lz=10, R=3.0, Uw=0.01, G=3.1, eta_M=0.4, visco_phase=0, sigma=0.0592)]
     rhos = [synth.droplet_densities(p.Lx, p.Ly, p.Lz, p.R, seed=30 + k) for k, p in enumerate(ps)]
     batch = L.Solver(ps)
+    batch.tune(kernel[1], 0, kernel[0])
     for k, r in enumerate(rhos):
         batch.init(k, r)
     batch.step(25)
     for k, (p, r) in enumerate(zip(ps, rhos)):
         solo = L.Solver(p)
+        solo.tune(kernel[1], 0, kernel[0])
         solo.init(0, r)
         solo.step(25)
         assert np.array_equal(batch.get_field(k, L.FIELD_F), solo.get_field(0, L.FIELD_F)), k
