@@ -136,7 +136,7 @@ size_t lbfe_params_size(void);
 size_t lbfe_obs_size(void);
 
 /* Validate p and fill the derived numbers.  BAD_PARAM on: a non-positive
- * lattice size, Lz < 2, Lx > 4096, more than 2^26 cells in one instance
+ * lattice size, Lz < 2, Lx > 4096, Ly or Lz > 65535, more than 2^26 cells in one instance
  * (larger boxes: split into a batch), a solvent viscosity <= 0 (eta_P too large), BGK
  * tau <= 1/2, tau_P <= 0, L^2 <= 3, Uw >= 0.1 (Mach limit), an unknown
  * phase or precision.  out may be NULL. */
@@ -172,7 +172,7 @@ lbfe_status lbfe_get_field(lbfe_handle *h, int k, int which, void *host_dst, siz
 lbfe_status lbfe_set_field(lbfe_handle *h, int k, int which, const void *host_src, size_t bytes);
 
 /* Number of kernel launches one lbfe_step(h, 1) enqueues: one per group of
- * up to 56 instances (the step kernel carries the instance descriptors in
+ * up to 64 instances (the step kernel carries the instance descriptors in
  * its parameter space). */
 int lbfe_launches_per_step(const lbfe_handle *h);
 

@@ -51,7 +51,7 @@ struct Derived {
 // (eta_d = eta_A, eta_M = eta_B + eta'_P).  Kinematic viscosities use the
 // bulk total density rho_in + rho_out.
 lbfe_status derive(const lbfe_params &p, Derived &d) {
-    if (p.Lx < 1 || p.Ly < 1 || p.Lz < 2 || p.Lx > 4096) return LBFE_ERR_BAD_PARAM;
+    if (p.Lx < 1 || p.Ly < 1 || p.Lz < 2 || p.Lx > 4096 || p.Ly > 65535 || p.Lz > 65535) return LBFE_ERR_BAD_PARAM;
     // the step kernel addresses fields with 32-bit offsets: (s*19 + i)*S + n < 2^32
     if ((long long)p.Lx * p.Ly * p.Lz > (1LL << 26)) return LBFE_ERR_BAD_PARAM;
     if (p.precision < LBFE_FP32 || p.precision > LBFE_BF16_OFFSET) return LBFE_ERR_BAD_PARAM;

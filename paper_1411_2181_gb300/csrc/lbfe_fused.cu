@@ -16,6 +16,9 @@ k_fused(const __grid_constant__ StepArgs A) {
     constexpr int TX = Gm::TX, NT = Gm::NT, RX = Gm::RX, RY = Gm::RY, R2N = Gm::R2N, MH = Gm::MH;
     using St = Stage<T, TY>;
     using Rg = Ring<TY>;
+    // interior planes take a push without the bounce-back selection where
+    // registers allow the second copy of the collision
+    constexpr bool kSplitWalls = TY <= 8;
     __shared__ u32 s_rows[RY];   // in-plane offsets of the radius-2 rows (wrapped)
     __shared__ u32 s_cols[RX];   // x of the radius-2 columns (wrapped)
     __shared__ u32 s_tmem;       // TMEM base address of the block
@@ -148,7 +151,7 @@ k_fused(const __grid_constant__ StepArgs A) {
                         m_load<T>(I, fin, Cin, S, pl + ofs_in, m);
                     }
                     m_store<TY>(I, m, idx_in, L.r3[2], ring2(p), L.cf[2]);
-                    tm_store38(tm_warp + (u32)((p & 1) * 64), m.f);
+                    tm_store38(tm_warp + (u32)((p & 1) * 64), reinterpret_cast<const float *>(m.ab));
                 }
                 if (St::REGION) {
 #pragma unroll
@@ -185,15 +188,15 @@ k_fused(const __grid_constant__ StepArgs A) {
             // ---------------- stage X(q): collision + push streaming (own cell only:
             // needs no barrier after stage F)
             if (q >= z0 && q < z1) {
-                float fx[2 * Q];
-                tm_load38(tm_warp + (u32)((q & 1) * 64), fx);   // whole warp
+                float2 fx[Q];
+                tm_load38(tm_warp + (u32)((q & 1) * 64), reinterpret_cast<float *>(fx));   // whole warp
                 if (valid) {
                     const u32 nq = (u32)(q * LxLy) + ofs_in;
                     const float rt = rAo + rBo;
                     if (!(rt > 0.f) || uo[0] != uo[0] || uo[1] != uo[1] || uo[2] != uo[2])
                         raise_step_flag(A.status, I, kFlagDiverged);
-                    const float nu = (rAo * I.nu_A + rBo * I.nu_B) / rt;
-                    const float om = 1.0f / (3.0f * nu + 0.5f);
+                    // omega = 1 / (3 nu + 1/2), nu = (rho_A nu_A + rho_B nu_B) / rho
+                    const float om = rt / (3.0f * (rAo * I.nu_A + rBo * I.nu_B) + 0.5f * rt);
                     const bool bottom = q == 0, top = q == Lz - 1;
                     PushOffsets Po;
                     const float2 *rho_s = reinterpret_cast<const float2 *>(smem() + Rg::RHO);
@@ -201,15 +204,19 @@ k_fused(const __grid_constant__ StepArgs A) {
                     Po.ring[1] = rho_s + L.r3[1] * R2N;
                     Po.ring[2] = rho_s + L.r3[2] * R2N;
                     Po.idx = idx_in;
-                    Po.own[0] = rAo;
-                    Po.own[1] = rBo;
+                    Po.own = make_float2(rAo, rBo);
                     Po.track = I.dens_out != nullptr;
-                    Po.r0[0] = I.rho0A;
-                    Po.r0[1] = I.rho0B;
-                    collide_push<T, RX>(fx, fout, S, 0, rAo, Po, uo, FA, om, nq, bottom, top, Uw, LxLy, dxy);
-                    collide_push<T, RX>(fx + Q, fout, S, 1, rBo, Po, uo, FB, om, nq, bottom, top, Uw, LxLy, dxy);
+                    Po.r0 = make_float2(I.rho0A, I.rho0B);
+                    const float2 F2[3] = {make_float2(FA[0], FB[0]), make_float2(FA[1], FB[1]),
+                                          make_float2(FA[2], FB[2])};
+                    if (!kSplitWalls || bottom || top)
+                        collide_push_ab<T, true, RX>(fx, fout, S, Po.own, Po, uo, F2, om, nq, bottom, top, Uw, LxLy,
+                                                     dxy);
+                    else
+                        collide_push_ab<T, false, RX>(fx, fout, S, Po.own, Po, uo, F2, om, nq, false, false, Uw,
+                                                      LxLy, dxy);
                     // this step's densities: the offsets of the state just written
-                    if (Store<T>::offset && Po.track) I.dens_out[nq] = make_float2(rAo, rBo);
+                    if (Store<T>::offset && Po.track) I.dens_out[nq] = Po.own;
                 }
             }
             __syncthreads();  // u of plane q complete on the radius-1 region
@@ -246,14 +253,14 @@ void fill_inst(StepInst &d, const InstDev &I, const PopMaps *maps, int cur) {
         d.c_map = maps->c[cur];
         d.tma = 1;
     }
-    d.Lx = I.Lx;
-    d.Ly = I.Ly;
-    d.Lz = I.Lz;
-    d.LxLy = I.Lx * I.Ly;
-    d.visc_comp = I.visc_comp;
-    d.ntx = I.ntx;
-    d.nty = I.nty;
-    d.zc = I.zc;
+    d.Lx = (unsigned short)I.Lx;
+    d.Ly = (unsigned short)I.Ly;
+    d.Lz = (unsigned short)I.Lz;
+    d.LxLy = (u32)(I.Lx * I.Ly);
+    d.visc_comp = (signed char)I.visc_comp;
+    d.ntx = (unsigned short)I.ntx;
+    d.nty = (unsigned short)I.nty;
+    d.zc = (unsigned short)I.zc;
     d.S = (u32)I.S;
     d.fin = I.f[cur];
     d.fout = I.f[cur ^ 1];

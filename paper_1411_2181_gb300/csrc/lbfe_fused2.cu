@@ -25,13 +25,6 @@ using PG = Geom<PTY>;                         // region and ring geometry of the
 constexpr int NPAIR_HALO = 4 * 18 + 2 * PTY;  // radius-2 region pairs outside the tile
 constexpr int P_TMEM_COLS = 512;              // 8 warps, two per lane quarter, 256 columns each
 
-// ---------------------------------------------------------------- packed FP32
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
-__device__ __forceinline__ float2 bc(float s) { return make_float2(s, s); }
-
 // Pair access of two adjacent elements of one population array.
 template <typename T>
 struct Pair;

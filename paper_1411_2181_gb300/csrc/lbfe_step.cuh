@@ -47,7 +47,7 @@
 //    issues no global loads, and the register file does not hold the
 //    populations across the stencil stages.
 //  * The instance descriptors travel in the kernel parameter space (up to
-//    56 instances per launch): scalars and pointers come from the constant
+//    64 instances per launch): scalars and pointers come from the constant
 //    bank instead of per-use global loads.
 #pragma once
 
@@ -60,17 +60,13 @@ namespace lbfe {
 typedef unsigned int u32;
 
 // ---------------------------------------------------------------- descriptors
-constexpr int kStepMaxInst = 56;
+constexpr int kStepMaxInst = 64;
 
 // Per-instance descriptor of one launch (kernel parameter space).
 struct StepInst {
     CUtensorMap pop_map;           // (x, y, z, population) view of fin (when tma): box of the tile's
                                    // own 32 x TY cells (TY = 16), or of its radius-2 region (TY <= 12)
     CUtensorMap c_map;             // (x, y, z, component) view of Cin, region box (TY <= 12)
-    int tma;                       // populations (and C) by TMA
-    int Lx, Ly, Lz, LxLy;
-    int visc_comp, ntx, nty, zc;   // visc_comp: 0 (A), 1 (B), -1 Newtonian
-    u32 S, pad_;                   // field stride
     const void *fin;               // populations read (state t)
     void *fout;                    // populations written (state t + 1)
     const float *Cin;
@@ -79,7 +75,12 @@ struct StepInst {
     float2 *dens_out;              // offsets of the state written
     unsigned *status;              // per-instance status word (may be null)
     float G, Uw, nu_A, nu_B, pi_coef, L2, inv_tauP, gx, gy, gz, rho0A, rho0B;
+    u32 S, LxLy;                   // field stride, cells per plane
+    unsigned short Lx, Ly, Lz, ntx, nty, zc;
+    signed char visc_comp;         // 0 (A), 1 (B), -1 Newtonian
+    signed char tma;               // populations (and C) by TMA
 };
+static_assert(sizeof(StepInst) == 384, "two tensor maps and 128 bytes of scalars");
 
 // One launch covers up to kStepMaxInst instances.  A single instance takes
 // the same kernel as a batch, so that batching never changes the arithmetic
@@ -234,7 +235,8 @@ __device__ __forceinline__ void tm_wait_ld38(u32 *r) {
                  );
 }
 
-// The 38 populations of a cell: columns [0, 38) of a plane buffer.
+// The 38 populations of a cell: columns [0, 38) of a plane buffer, in the
+// order (A_0, B_0, A_1, B_1, ...).
 __device__ __forceinline__ void tm_store38(u32 taddr, const float *v) {
     tm_st32(taddr, v);
     tm_st4(taddr + 32, v + 32);
@@ -261,13 +263,6 @@ __device__ __forceinline__ int wrapg(int a, int L) { a %= L; return a < 0 ? a + 
 // symmetric-tensor slot of (a, b): xx, yy, zz, xy, xz, yz
 __host__ __device__ constexpr int symk(int a, int b) {
     return a == b ? a : ((a + b) == 1 ? 3 : ((a + b) == 2 ? 4 : 5));
-}
-
-template <typename T>
-__device__ __forceinline__ float ldpop(const T *p, float add) {
-    float v = Store<T>::ld(p);
-    if (Store<T>::offset) v += add;
-    return v;
 }
 
 // Cell h (0 <= h < NRING1) of the radius-1 region outside the tile.
@@ -338,33 +333,42 @@ struct Stage {
 extern __shared__ float4 lbfe_smem4[];
 __device__ __forceinline__ float *smem() { return reinterpret_cast<float *>(lbfe_smem4); }
 
+// Packed FP32 (two lanes per instruction).
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 bc(float s) { return make_float2(s, s); }
+
 // Stage M inputs of one cell: its 38 populations (decoded to FP32) and 6
 // conformation components.
+// Stage M inputs of one cell: its populations as (component A, component B)
+// pairs (decoded to FP32) and 6 conformation components.  The pairs feed
+// packed FP32 arithmetic (two lanes per instruction) in stages M and X.
 struct MCell {
-    float f[2 * Q];
+    float2 ab[Q];
     float c[6];
 };
+
+// Storage offsets (rho0_A, rho0_B) of cell n for the reduced forms.
+template <typename T>
+__device__ __forceinline__ float2 cell_offsets(const StepInst &I, u32 n) {
+    if (!Store<T>::offset) return make_float2(0.f, 0.f);
+    if (I.dens_in) return __ldg(I.dens_in + n);
+    return make_float2(I.rho0A, I.rho0B);
+}
 
 // Cell offsets are 32-bit: an instance holds at most 2^26 cells, so every
 // field offset (s*19 + i)*S + n stays below 2^32.
 template <typename T>
 __device__ __forceinline__ void m_load(const StepInst &I, const T *__restrict__ fin, const float *__restrict__ Cin,
                                        u32 S, u32 n, MCell &m) {
-    float ra0 = 0.f, rb0 = 0.f;
-    if (Store<T>::offset) {
-        if (I.dens_in) {
-            const float2 od = __ldg(I.dens_in + n);
-            ra0 = od.x;
-            rb0 = od.y;
-        } else {
-            ra0 = I.rho0A;
-            rb0 = I.rho0B;
-        }
-    }
+    const float2 o = cell_offsets<T>(I, n);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        m.f[i] = ldpop(fin + (u32)(i * S + n), wq(i) * ra0);
-        m.f[Q + i] = ldpop(fin + (u32)((Q + i) * S + n), wq(i) * rb0);
+        m.ab[i].x = Store<T>::ld(fin + (u32)(i * S + n));
+        m.ab[i].y = Store<T>::ld(fin + (u32)((Q + i) * S + n));
+        if (Store<T>::offset) m.ab[i] = fma2(bc(wq(i)), o, m.ab[i]);
     }
 #pragma unroll
     for (int k = 0; k < 6; ++k) m.c[k] = __ldg(Cin + (u32)(k * S + n));
@@ -375,25 +379,12 @@ __device__ __forceinline__ void m_load(const StepInst &I, const T *__restrict__ 
 template <typename T, int NT>
 __device__ __forceinline__ void m_load_staged(const StepInst &I, const T *stage, int t,
                                               const float *__restrict__ Cin, u32 S, u32 n, MCell &m) {
-    float ra0 = 0.f, rb0 = 0.f;
-    if (Store<T>::offset) {
-        if (I.dens_in) {
-            const float2 od = __ldg(I.dens_in + n);
-            ra0 = od.x;
-            rb0 = od.y;
-        } else {
-            ra0 = I.rho0A;
-            rb0 = I.rho0B;
-        }
-    }
+    const float2 o = cell_offsets<T>(I, n);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        m.f[i] = Store<T>::ld_plain(stage + i * NT + t);
-        m.f[Q + i] = Store<T>::ld_plain(stage + (Q + i) * NT + t);
-        if (Store<T>::offset) {
-            m.f[i] += wq(i) * ra0;
-            m.f[Q + i] += wq(i) * rb0;
-        }
+        m.ab[i].x = Store<T>::ld_plain(stage + i * NT + t);
+        m.ab[i].y = Store<T>::ld_plain(stage + (Q + i) * NT + t);
+        if (Store<T>::offset) m.ab[i] = fma2(bc(wq(i)), o, m.ab[i]);
     }
 #pragma unroll
     for (int k = 0; k < 6; ++k) m.c[k] = __ldg(Cin + (u32)(k * S + n));
@@ -404,26 +395,13 @@ template <typename T, int TY>
 __device__ __forceinline__ void m_load_region(const StepInst &I, const T *sp, const float *sc, int gx, int gy, u32 n,
                                               MCell &m) {
     using St = Stage<T, TY>;
-    float ra0 = 0.f, rb0 = 0.f;
-    if (Store<T>::offset) {
-        if (I.dens_in) {
-            const float2 od = __ldg(I.dens_in + n);
-            ra0 = od.x;
-            rb0 = od.y;
-        } else {
-            ra0 = I.rho0A;
-            rb0 = I.rho0B;
-        }
-    }
+    const float2 o = cell_offsets<T>(I, n);
     const int e = gy * St::BW + gx - 2 + St::XPAD;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        m.f[i] = Store<T>::ld_plain(sp + i * St::POP_PLANE + e);
-        m.f[Q + i] = Store<T>::ld_plain(sp + (Q + i) * St::POP_PLANE + e);
-        if (Store<T>::offset) {
-            m.f[i] += wq(i) * ra0;
-            m.f[Q + i] += wq(i) * rb0;
-        }
+        m.ab[i].x = Store<T>::ld_plain(sp + i * St::POP_PLANE + e);
+        m.ab[i].y = Store<T>::ld_plain(sp + (Q + i) * St::POP_PLANE + e);
+        if (Store<T>::offset) m.ab[i] = fma2(bc(wq(i)), o, m.ab[i]);
     }
     const int ec = gy * 40 + gx + 2;
 #pragma unroll
@@ -431,7 +409,9 @@ __device__ __forceinline__ void m_load_region(const StepInst &I, const T *sp, co
 }
 
 // Stage M for one cell: moments, stress scalars and conformation into the
-// ring slots of its plane.
+// ring slots of its plane.  Both components' sums run as packed pairs; the
+// momentum is summed from opposite-pair differences f_i - f_opp(i) (exact
+// in FP32 per pair), per component, and the components added at the end.
 template <int TY>
 __device__ __forceinline__ void m_store(const StepInst &I, const MCell &m, int idx, int s3, int s2, int s4) {
     // s3: rho / stress slot, s2: j slot, s4: C slot of the plane
@@ -441,27 +421,26 @@ __device__ __forceinline__ void m_store(const StepInst &I, const MCell &m, int i
     float *pi_s = smem() + Rg::PI + s3 * 2 * R2N;
     float *j_s = smem() + Rg::J + s2 * 3 * R2N;
     float *c_s = smem() + Rg::C + s4 * 6 * R2N;
-    float rA = 0.f, rB = 0.f;
+    float2 r = m.ab[0];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) { rA += m.f[i]; rB += m.f[Q + i]; }
-    // momentum from opposite-pair differences (exact in FP32 per pair)
-    float jx = 0.f, jy = 0.f, jz = 0.f;
+    for (int i = 1; i < Q; ++i) r = add2(r, m.ab[i]);
+    float2 jx = bc(0.f), jy = jx, jz = jx;
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {
-        const float d = (m.f[i] - m.f[i + 1]) + (m.f[Q + i] - m.f[Q + i + 1]);
-        if (cx(i)) jx += cx(i) * d;
-        if (cy(i)) jy += cy(i) * d;
-        if (cz(i)) jz += cz(i) * d;
+        const float2 d = sub2(m.ab[i], m.ab[i + 1]);
+        if (cx(i)) jx = cx(i) > 0 ? add2(jx, d) : sub2(jx, d);
+        if (cy(i)) jy = cy(i) > 0 ? add2(jy, d) : sub2(jy, d);
+        if (cz(i)) jz = cz(i) > 0 ? add2(jz, d) : sub2(jz, d);
     }
-    rho_s[idx] = make_float2(rA, rB);
-    j_s[idx] = jx;
-    j_s[R2N + idx] = jy;
-    j_s[2 * R2N + idx] = jz;
+    rho_s[idx] = r;
+    j_s[idx] = jx.x + jx.y;
+    j_s[R2N + idx] = jy.x + jy.y;
+    j_s[2 * R2N + idx] = jz.x + jz.y;
 #pragma unroll
     for (int k = 0; k < 6; ++k) c_s[k * R2N + idx] = m.c[k];
     float a = 0.f, fp = 1.f;
     if (I.visc_comp >= 0) {
-        a = I.pi_coef * (I.visc_comp == 0 ? rA : rB) / (rA + rB);
+        a = I.pi_coef * (I.visc_comp == 0 ? r.x : r.y) / (r.x + r.y);
         fp = peterlin(I.L2, m.c[0], m.c[1], m.c[2]);
     }
     pi_s[idx] = a * fp;
@@ -594,89 +573,109 @@ __device__ __forceinline__ bool stage_u_cell(const StepInst &I, int idx, const S
 }
 
 // Offsets of the reduced storage forms at the destination of a push:
-// the destination cell's densities of this step (from the density ring of
-// planes q-1, q, q+1), or the constant offsets when densities are not
-// tracked.
+// the destination cell's densities (rho_A, rho_B) of this step (from the
+// density ring of planes q-1, q, q+1), or the constant offsets when
+// densities are not tracked.
 struct PushOffsets {
     const float2 *ring[3];   // density ring slots of planes q-1, q, q+1
     int idx;                 // ring index of the pushing cell
-    float own[2];            // the pushing cell's densities
+    float2 own;              // the pushing cell's densities
     bool track;
-    float r0[2];             // constant offsets
+    float2 r0;               // constant offsets
 };
 
 template <int RX>
-__device__ __forceinline__ float push_offset(const PushOffsets &P, int s, int d, bool wall) {
-    if (!P.track) return P.r0[s];
-    if (wall) return P.own[s];
-    const float2 v = P.ring[cz(d) + 1][P.idx + cx(d) + cy(d) * RX];
-    return s == 0 ? v.x : v.y;
+__device__ __forceinline__ float2 push_offset(const PushOffsets &P, int d, bool wall) {
+    if (!P.track) return P.r0;
+    if (wall) return P.own;
+    return P.ring[cz(d) + 1][P.idx + cx(d) + cy(d) * RX];
 }
 
-// Store post-collision population d of the cell at offset n into its
-// streamed position x + c_d.  A population whose target lies beyond a wall returns into the cell as the opposite direction (halfway
-// bounce-back) with the moving-wall term -6 w_d rho_s (c_d . U_wall).
-template <typename T, int RX>
-__device__ __forceinline__ void push_one(T *__restrict__ fdst, u32 S, int s, int d, float v, float rs,
-                                         const PushOffsets &P, u32 n, bool bottom, bool top, float Uw, int LxLy,
-                                         const int dxy[3][3]) {
+// Store post-collision population d of both components (lanes x: A, y: B)
+// of the cell at offset n into its streamed position x + c_d.  With WALLS,
+// a population whose target lies beyond a wall returns into the cell as the
+// opposite direction (halfway bounce-back) with the moving-wall term
+// -6 w_d rho_s (c_d . U_wall).
+template <typename T, bool WALLS, int RX>
+__device__ __forceinline__ void push_ab(T *__restrict__ fdst, u32 S, int d, float2 v, float2 rs,
+                                        const PushOffsets &P, u32 n, bool bottom, bool top, float Uw, int LxLy,
+                                        const int dxy[3][3]) {
     int dir = d;
     u32 dst = n + (u32)(cz(d) * LxLy + dxy[cx(d) + 1][cy(d) + 1]);
     bool wall = false;
-    if ((cz(d) < 0 && bottom) || (cz(d) > 0 && top)) {
-        v -= 6.f * wq(d) * rs * (float)cx(d) * (cz(d) < 0 ? -Uw : Uw);
+    if (WALLS && ((cz(d) < 0 && bottom) || (cz(d) > 0 && top))) {
+        v = fma2(bc(-6.f * wq(d) * (float)cx(d) * (cz(d) < 0 ? -Uw : Uw)), rs, v);
         dir = opp(d);
         dst = n;
         wall = true;
     }
-    if (Store<T>::offset) v -= wq(d) * push_offset<RX>(P, s, d, wall);
-    Store<T>::st(fdst + (u32)((s * Q + dir) * S + dst), v);
+    if (Store<T>::offset) v = fma2(bc(-wq(d)), push_offset<RX>(P, d, wall), v);
+    Store<T>::st(fdst + (u32)(dir * S + dst), v.x);
+    Store<T>::st(fdst + (u32)((Q + dir) * S + dst), v.y);
 }
 
-// BGK + Guo collision of one component at one cell and push streaming of
-// its 19 populations.  Opposite directions share the symmetric parts:
+// BGK + Guo collision of both components of one cell, on packed FP32 (lane
+// x: component A, lane y: component B), and push streaming.  Opposite
+// directions share the symmetric parts:
 //   f^eq_{i,-i} = w rho (1 + 9/2 (c.u)^2 - 3/2 u.u) +- 3 w rho (c.u)
 //   S_{i,-i}    = (1 - 1/2tau) w (9 (c.u)(c.F) - 3 u.F) +- 3 (1 - 1/2tau) w (c.F)
 // so that with E = omega rho (1 - 3/2 u.u) - 3 (1 - 1/2tau) u.F the
 // post-collision pair is (1 - omega) f_{i,-i} + sym +- anti,
 //   sym  = w E + (c.u) (9/2 omega rho w (c.u) + 9 (1 - 1/2tau) w (c.F)),
 //   anti = 3 omega rho w (c.u) + 3 (1 - 1/2tau) w (c.F),
-// with the weight products formed once per weight class.
-template <typename T, int RX>
-__device__ __forceinline__ void collide_push(const float *fv, T *__restrict__ fdst, u32 S, int s, float rs,
-                                             const PushOffsets &P, const float u[3], const float F[3], float om, u32 n,
-                                             bool bottom, bool top, float Uw, int LxLy, const int dxy[3][3]) {
+// with the weight products formed once per weight class.  u and omega are
+// common to both components; rho and F are per component.
+template <typename T, bool WALLS, int RX>
+__device__ __forceinline__ void collide_push_ab(const float2 *fv, T *__restrict__ fdst, u32 S, float2 rs,
+                                                const PushOffsets &P, const float u[3], const float2 F[3], float om,
+                                                u32 n, bool bottom, bool top, float Uw, int LxLy,
+                                                const int dxy[3][3]) {
     const float omc = 1.0f - om, pref = 1.0f - 0.5f * om;
     const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    const float uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
-    const float E = om * (rs * (1.f - 1.5f * uu)) - 3.f * pref * uF;
-    const float a1 = 4.5f * om * rs, b1 = 9.f * pref, a2 = 3.f * om * rs, b2 = 3.f * pref;
+    const float2 u2[3] = {bc(u[0]), bc(u[1]), bc(u[2])};
+    const float2 uF = fma2(u2[2], F[2], fma2(u2[1], F[1], mul2(u2[0], F[0])));
+    const float2 E = fma2(bc(-3.f * pref), uF, mul2(bc(om * (1.f - 1.5f * uu)), rs));
+    const float2 omc2 = bc(omc);
     {
-        float v = omc * fv[0] + wq(0) * E;
-        if (Store<T>::offset) v -= wq(0) * (P.track ? P.own[s] : P.r0[s]);
-        Store<T>::st(fdst + (u32)(s * Q * S + n), v);
+        float2 v = fma2(omc2, fv[0], mul2(bc(wq(0)), E));
+        if (Store<T>::offset) v = fma2(bc(-wq(0)), P.track ? P.own : P.r0, v);
+        Store<T>::st(fdst + n, v.x);
+        Store<T>::st(fdst + (u32)(Q * S + n), v.y);
     }
     // weight classes: faces (i = 1..6) and edges (i = 7..18)
-    float Ew[2], a1w[2], b1w[2], a2w[2], b2w[2];
+    float2 Ew[2], a1w[2], b1w[2], a2w[2], b2w[2];
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
         const float w = wq(c == 0 ? 1 : 7);
-        Ew[c] = w * E;
-        a1w[c] = w * a1;
-        b1w[c] = w * b1;
-        a2w[c] = w * a2;
-        b2w[c] = w * b2;
+        Ew[c] = mul2(bc(w), E);
+        a1w[c] = mul2(bc(4.5f * om * w), rs);
+        b1w[c] = bc(9.f * pref * w);
+        a2w[c] = mul2(bc(3.f * om * w), rs);
+        b2w[c] = bc(3.f * pref * w);
     }
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {
         const int c = i <= 6 ? 0 : 1;
-        const float cu = cx(i) * u[0] + cy(i) * u[1] + cz(i) * u[2];
-        const float cF = cx(i) * F[0] + cy(i) * F[1] + cz(i) * F[2];
-        const float sym = fmaf(cu, fmaf(a1w[c], cu, b1w[c] * cF), Ew[c]);
-        const float anti = fmaf(a2w[c], cu, b2w[c] * cF);
-        push_one<T, RX>(fdst, S, s, i, fmaf(omc, fv[i], sym + anti), rs, P, n, bottom, top, Uw, LxLy, dxy);
-        push_one<T, RX>(fdst, S, s, i + 1, fmaf(omc, fv[i + 1], sym - anti), rs, P, n, bottom, top, Uw,
-                               LxLy, dxy);
+        float2 cu = bc(0.f), cF = cu;
+        bool first = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int ca = a == 0 ? cx(i) : (a == 1 ? cy(i) : cz(i));
+            if (!ca) continue;
+            if (first) {
+                cu = ca > 0 ? u2[a] : mul2(bc(-1.f), u2[a]);
+                cF = ca > 0 ? F[a] : mul2(bc(-1.f), F[a]);
+                first = false;
+            } else {
+                cu = ca > 0 ? add2(cu, u2[a]) : sub2(cu, u2[a]);
+                cF = ca > 0 ? add2(cF, F[a]) : sub2(cF, F[a]);
+            }
+        }
+        const float2 sym = fma2(cu, fma2(a1w[c], cu, mul2(b1w[c], cF)), Ew[c]);
+        const float2 anti = fma2(a2w[c], cu, mul2(b2w[c], cF));
+        push_ab<T, WALLS, RX>(fdst, S, i, fma2(omc2, fv[i], add2(sym, anti)), rs, P, n, bottom, top, Uw, LxLy, dxy);
+        push_ab<T, WALLS, RX>(fdst, S, i + 1, fma2(omc2, fv[i + 1], sub2(sym, anti)), rs, P, n, bottom, top, Uw,
+                              LxLy, dxy);
     }
 }
 
