@@ -19,6 +19,9 @@ k_fused(const __grid_constant__ StepArgs A) {
     // interior planes take a push without the bounce-back selection where
     // registers allow the second copy of the collision
     constexpr bool kSplitWalls = TY <= 8;
+    // the collision's TMEM loads are issued before stage F where registers
+    // allow holding them through it
+    constexpr bool kEarlyTmem = TY <= 8;
     __shared__ u32 s_rows[RY];   // in-plane offsets of the radius-2 rows (wrapped)
     __shared__ u32 s_cols[RX];   // x of the radius-2 columns (wrapped)
     __shared__ u32 s_tmem;       // TMEM base address of the block
@@ -43,13 +46,29 @@ k_fused(const __grid_constant__ StepArgs A) {
     // this warp's TMEM slot: lane quarter ty % 4, columns (ty / 4) * 128
     const u32 tm_warp = s_tmem + ((u32)(32 * (ty & 3)) << 16) + (u32)((ty >> 2) * 128);
 
-    // the first plane of the block's first item
-    if (t == 0 && blockIdx.x < A.total_items) {
-        const ItemPos P0 = item_pos<TY>(A, blockIdx.x);
-        if (A.inst[P0.k].tma) issue_plane<T, TY>(A, P0, P0.z0 - 2, stage_addr, bar);
+    // Block b starts with item b (neighbouring tiles on neighbouring blocks,
+    // which share their halos through L2); further items come from the
+    // launch's counter, one ahead: the next item is known while the current
+    // one runs, so that its first plane can be copied early, and blocks
+    // that finish early take more items.
+    __shared__ int s_item[2];
+    if (t == 0) {
+        const int first = blockIdx.x;
+        s_item[0] = first;
+        // the first plane of the block's first item
+        if (first < A.total_items) {
+            const ItemPos P0 = item_pos<TY>(A, first);
+            if (A.inst[P0.k].tma) issue_plane<T, TY>(A, P0, P0.z0 - 2, stage_addr, bar);
+        }
     }
-
-    for (int item = blockIdx.x; item < A.total_items; item += gridDim.x) {
+    __syncthreads();
+    int slot = 0;
+    for (int item = s_item[0]; item < A.total_items;) {
+        // the next item: taken now, published after the first stage M (the
+        // item-start barriers do not wait for the atomic)
+        // (a launch with no more items than blocks has no further items)
+        int next_t0 = A.total_items;
+        if (t == 0 && A.total_items > (int)gridDim.x) next_t0 = (int)(gridDim.x + atomicAdd(A.work, 1u));
         const ItemPos P = item_pos<TY>(A, item);
         const int k = P.k;
         const StepInst &I = A.inst[k];
@@ -167,13 +186,25 @@ k_fused(const __grid_constant__ StepArgs A) {
             // the staging buffer is free: start the copy of the next plane
             // (of this item, else of the block's next item)
             if (t == 0) {
+                if (p == z0 - 2) s_item[slot ^ 1] = next_t0;
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 if (p < z1 + 1) {
                     if (tma) issue_plane<T, TY>(A, P, p + 1, stage_addr, bar);
-                } else if (item + (int)gridDim.x < A.total_items) {
-                    const ItemPos Pn = item_pos<TY>(A, item + gridDim.x);
+                } else if (next_t0 < A.total_items) {
+                    const ItemPos Pn = item_pos<TY>(A, next_t0);
                     if (A.inst[Pn.k].tma) issue_plane<T, TY>(A, Pn, Pn.z0 - 2, stage_addr, bar);
                 }
+            }
+            // the collision's populations start to come back from TMEM here (or
+            // just before the collision) and are waited for after stage F
+            const bool doX = q >= z0 && q < z1;
+            u32 tr[38];
+            if (kEarlyTmem && doX) {
+                const u32 ta = tm_warp + (u32)((q & 1) * 64);
+                tm_wait_st();
+                tm_ld32(ta, tr);
+                tm_ld4(ta + 32, tr + 32);
+                tm_ld2(ta + 36, tr + 36);
             }
             // ---------------- stage F(q): radius-1 region
             if (q >= max(z0 - 1, 0) && q <= min(z1, Lz - 1)) {
@@ -187,9 +218,18 @@ k_fused(const __grid_constant__ StepArgs A) {
             }
             // ---------------- stage X(q): collision + push streaming (own cell only:
             // needs no barrier after stage F)
-            if (q >= z0 && q < z1) {
+            if (doX) {
+                if (!kEarlyTmem) {
+                    const u32 ta = tm_warp + (u32)((q & 1) * 64);
+                    tm_wait_st();
+                    tm_ld32(ta, tr);
+                    tm_ld4(ta + 32, tr + 32);
+                    tm_ld2(ta + 36, tr + 36);
+                }
+                tm_wait_ld38(tr);
                 float2 fx[Q];
-                tm_load38(tm_warp + (u32)((q & 1) * 64), reinterpret_cast<float *>(fx));   // whole warp
+#pragma unroll
+                for (int i = 0; i < Q; ++i) fx[i] = make_float2(__uint_as_float(tr[2 * i]), __uint_as_float(tr[2 * i + 1]));
                 if (valid) {
                     const u32 nq = (u32)(q * LxLy) + ofs_in;
                     const float rt = rAo + rBo;
@@ -230,8 +270,11 @@ k_fused(const __grid_constant__ StepArgs A) {
             }
             __syncthreads();  // stage U done with the rings before stage M(p+1)
         }
+        item = s_item[slot ^ 1];   // published in the first iteration, several barriers ago
+        slot ^= 1;
     }
 
+    if (t == 0 && A.total_items > (int)gridDim.x) release_work_counters(A.work);
     if (!waits_ok) {
         // a copy may still be in flight: give it one more bounded wait
         mbar_wait(bar, parity);
@@ -349,6 +392,7 @@ cudaError_t fused_group(const LaunchCtx &c, int cur, int k0, int k1) {
     StepArgs a{};
     a.n = k1 - k0;
     a.status = c.status;
+    a.work = c.status + 2;
     const int base = c.item_off_host[k0];
     for (int k = k0; k < k1; ++k) {
         a.item_off[k - k0] = c.item_off_host[k] - base;

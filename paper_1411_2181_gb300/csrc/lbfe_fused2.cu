@@ -30,14 +30,14 @@ template <typename T>
 struct Pair;
 template <>
 struct Pair<float> {
-    static __device__ __forceinline__ float2 ldg(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
+    static __device__ __forceinline__ float2 ldg(const float *p) { return __ldcg(reinterpret_cast<const float2 *>(p)); }
     static __device__ __forceinline__ float2 lds(const float *p) { return *reinterpret_cast<const float2 *>(p); }
     static __device__ __forceinline__ void stg(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
 };
 template <>
 struct Pair<__half> {
     static __device__ __forceinline__ float2 ldg(const __half *p) {
-        return __half22float2(__ldg(reinterpret_cast<const __half2 *>(p)));
+        return __half22float2(__ldcg(reinterpret_cast<const __half2 *>(p)));
     }
     static __device__ __forceinline__ float2 lds(const __half *p) {
         return __half22float2(*reinterpret_cast<const __half2 *>(p));
@@ -49,7 +49,7 @@ struct Pair<__half> {
 template <>
 struct Pair<__nv_bfloat16> {
     static __device__ __forceinline__ float2 ldg(const __nv_bfloat16 *p) {
-        return __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162 *>(p)));
+        return __bfloat1622float2(__ldcg(reinterpret_cast<const __nv_bfloat162 *>(p)));
     }
     static __device__ __forceinline__ float2 lds(const __nv_bfloat16 *p) {
         return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
@@ -164,7 +164,7 @@ __device__ __forceinline__ void pair_offsets(const StepInst &I, u32 n, float2 &r
     ra0 = rb0 = make_float2(0.f, 0.f);
     if (Store<T>::offset) {
         if (I.dens_in) {
-            const float4 od = __ldg(reinterpret_cast<const float4 *>(I.dens_in + n));
+            const float4 od = __ldcg(reinterpret_cast<const float4 *>(I.dens_in + n));
             ra0 = make_float2(od.x, od.z);
             rb0 = make_float2(od.y, od.w);
         } else {
@@ -399,12 +399,23 @@ __global__ void __launch_bounds__(PNT, 1) k_fused_pair(const __grid_constant__ S
     // this warp's TMEM columns: lane quarter warp % 4, 256 columns from (warp / 4) * 256
     const u32 tm_warp = s_tmem + ((u32)(32 * (warp & 3)) << 16) + (u32)((warp >> 2) * 256);
 
-    if (t == 0 && blockIdx.x < A.total_items) {
-        const ItemPos P0 = item_pos<PTY>(A, blockIdx.x);
-        if (A.inst[P0.k].tma) issue_plane<T, PTY>(A, P0, P0.z0 - 2, stage_addr, bar);
+    __shared__ int s_item[2];   // work items from the launch's counter, one ahead
+    if (t == 0) {
+        const int first = blockIdx.x;
+        s_item[0] = first;
+        if (first < A.total_items) {
+            const ItemPos P0 = item_pos<PTY>(A, first);
+            if (A.inst[P0.k].tma) issue_plane<T, PTY>(A, P0, P0.z0 - 2, stage_addr, bar);
+        }
     }
-
-    for (int item = blockIdx.x; item < A.total_items; item += gridDim.x) {
+    __syncthreads();
+    int slot = 0;
+    for (int item = s_item[0]; item < A.total_items;) {
+        // the next item: taken now, published after the first stage M (the
+        // item-start barriers do not wait for the atomic)
+        // (a launch with no more items than blocks has no further items)
+        int next_t0 = A.total_items;
+        if (t == 0 && A.total_items > (int)gridDim.x) next_t0 = (int)(gridDim.x + atomicAdd(A.work, 1u));
         const ItemPos P = item_pos<PTY>(A, item);
         const StepInst &I = A.inst[P.k];
         const int Lx = I.Lx, Ly = I.Ly, Lz = I.Lz;
@@ -493,11 +504,12 @@ __global__ void __launch_bounds__(PNT, 1) k_fused_pair(const __grid_constant__ S
             }
             __syncthreads();
             if (t == 0) {
+                if (p == z0 - 2) s_item[slot ^ 1] = next_t0;
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 if (p < z1 + 1) {
                     if (tma) issue_plane<T, PTY>(A, P, p + 1, stage_addr, bar);
-                } else if (item + (int)gridDim.x < A.total_items) {
-                    const ItemPos Pn = item_pos<PTY>(A, item + gridDim.x);
+                } else if (next_t0 < A.total_items) {
+                    const ItemPos Pn = item_pos<PTY>(A, next_t0);
                     if (A.inst[Pn.k].tma) issue_plane<T, PTY>(A, Pn, Pn.z0 - 2, stage_addr, bar);
                 }
             }
@@ -568,8 +580,11 @@ __global__ void __launch_bounds__(PNT, 1) k_fused_pair(const __grid_constant__ S
             }
             __syncthreads();
         }
+        item = s_item[slot ^ 1];   // published in the first iteration, several barriers ago
+        slot ^= 1;
     }
 
+    if (t == 0 && A.total_items > (int)gridDim.x) release_work_counters(A.work);
     if (!waits_ok) {
         mbar_wait(bar, parity);
         if (t == 0) atomicOr(A.status, kFlagTimeout);

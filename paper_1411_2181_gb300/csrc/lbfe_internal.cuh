@@ -37,22 +37,28 @@ __host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i 
 
 // Storage forms of the populations.  FP32 stores f itself; the reduced
 // forms store f - w_i rho0_s rounded to nearest even and decode in FP32.
+// ld_l2 reads through L2 only (no L1 allocation): the step kernels keep
+// most of the SM's L1/shared capacity as shared memory, and their few
+// ordinary loads are throttled when they compete for the small L1.
 template <typename T> struct Store;
 template <> struct Store<float> {
     static constexpr bool offset = false;
     static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ float ld_l2(const float *p) { return __ldcg(p); }
     static __device__ __forceinline__ float ld_plain(const float *p) { return *p; }
     static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
 };
 template <> struct Store<__half> {
     static constexpr bool offset = true;
     static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float ld_l2(const __half *p) { return __half2float(__ldcg(p)); }
     static __device__ __forceinline__ float ld_plain(const __half *p) { return __half2float(*p); }
     static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
 };
 template <> struct Store<__nv_bfloat16> {
     static constexpr bool offset = true;
     static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ float ld_l2(const __nv_bfloat16 *p) { return __bfloat162float(__ldcg(p)); }
     static __device__ __forceinline__ float ld_plain(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };

@@ -88,6 +88,7 @@ static_assert(sizeof(StepInst) == 384, "two tensor maps and 128 bytes of scalars
 struct StepArgs {
     int n, total_items;
     unsigned *status;              // status word of the launch
+    unsigned *work;                // [0] work-item counter, [1] finished blocks; zero between launches
     int item_off[kStepMaxInst + 1];  // first work item of each instance
     StepInst inst[kStepMaxInst];
 };
@@ -354,7 +355,7 @@ struct MCell {
 template <typename T>
 __device__ __forceinline__ float2 cell_offsets(const StepInst &I, u32 n) {
     if (!Store<T>::offset) return make_float2(0.f, 0.f);
-    if (I.dens_in) return __ldg(I.dens_in + n);
+    if (I.dens_in) return __ldcg(I.dens_in + n);
     return make_float2(I.rho0A, I.rho0B);
 }
 
@@ -366,12 +367,12 @@ __device__ __forceinline__ void m_load(const StepInst &I, const T *__restrict__ 
     const float2 o = cell_offsets<T>(I, n);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        m.ab[i].x = Store<T>::ld(fin + (u32)(i * S + n));
-        m.ab[i].y = Store<T>::ld(fin + (u32)((Q + i) * S + n));
+        m.ab[i].x = Store<T>::ld_l2(fin + (u32)(i * S + n));
+        m.ab[i].y = Store<T>::ld_l2(fin + (u32)((Q + i) * S + n));
         if (Store<T>::offset) m.ab[i] = fma2(bc(wq(i)), o, m.ab[i]);
     }
 #pragma unroll
-    for (int k = 0; k < 6; ++k) m.c[k] = __ldg(Cin + (u32)(k * S + n));
+    for (int k = 0; k < 6; ++k) m.c[k] = __ldcg(Cin + (u32)(k * S + n));
 }
 
 // As m_load, with the populations taken from the TMA staging buffer
@@ -676,6 +677,16 @@ __device__ __forceinline__ void collide_push_ab(const float2 *fv, T *__restrict_
         push_ab<T, WALLS, RX>(fdst, S, i, fma2(omc2, fv[i], add2(sym, anti)), rs, P, n, bottom, top, Uw, LxLy, dxy);
         push_ab<T, WALLS, RX>(fdst, S, i + 1, fma2(omc2, fv[i + 1], sub2(sym, anti)), rs, P, n, bottom, top, Uw,
                               LxLy, dxy);
+    }
+}
+
+// Called by every block once it has taken its last item: the last block to
+// finish returns the two counters to zero for the next launch (no other
+// block reads them any more).
+__device__ __forceinline__ void release_work_counters(unsigned *work) {
+    if (atomicAdd(work + 1, 1u) == gridDim.x - 1) {
+        work[0] = 0u;
+        work[1] = 0u;
     }
 }
 
