@@ -157,7 +157,11 @@ lbfe_status lbfe_create(lbfe_handle **h, const lbfe_params *p, int n, void *devi
  * start).  Resets the step counter.  Copies synchronously from host memory. */
 lbfe_status lbfe_init(lbfe_handle *h, int k, const double *rho_init);
 
-/* Advance every instance by nsteps time steps (asynchronous on the stream). */
+/* Advance every instance by nsteps time steps (asynchronous on the stream).
+ * With nsteps >= 2 the steps replay CUDA graphs of one step (captured once
+ * per launch shape on a private stream); results are identical to single
+ * steps.  Inside a stream capture of the caller the kernels are launched
+ * directly into it. */
 lbfe_status lbfe_step(lbfe_handle *h, long long nsteps);
 
 /* Observables of instance k (synchronises the stream). */

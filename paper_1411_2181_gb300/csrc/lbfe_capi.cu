@@ -220,6 +220,19 @@ struct lbfe_handle {
     unsigned *status = nullptr;
     double *mass = nullptr;
     int cur = 0;
+    // CUDA graphs of one time step from each parity of the ping-pong state,
+    // captured on a private stream and replayed by lbfe_step; dropped when
+    // the launch shape changes
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
+
+    void drop_graphs() {
+        for (auto &g : step_graph)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+    }
 
     lbfe::LaunchCtx ctx() const {
         lbfe::LaunchCtx c;
@@ -284,6 +297,7 @@ static lbfe_status configure_fused(lbfe_handle *h, int step_kernel, int tile_y, 
         if (off[k] + items > (long long)0x7fffffff) return LBFE_ERR_BAD_PARAM;
         off[k + 1] = off[k] + (int)items;
     }
+    h->drop_graphs();
     h->tile_y = tile_y;
     h->step_kernel = step_kernel;
     h->z_chunk_req = z_chunk;
@@ -457,13 +471,42 @@ lbfe_status lbfe_init(lbfe_handle *h, int k, const double *rho_init) {
     return LBFE_OK;
 }
 
+// Capture the launches of one step from state parity cur into a graph.
+static cudaError_t build_step_graph(lbfe_handle *h, int cur) {
+    cudaError_t e = cudaSuccess;
+    if (!h->cap_stream) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    lbfe::LaunchCtx c = h->ctx();
+    c.stream = h->cap_stream;
+    const cudaError_t el = lbfe::launch_fused(c, cur);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (el != cudaSuccess) e = el;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->step_graph[cur], g, 0);
+    if (g) cudaGraphDestroy(g);
+    return e;
+}
+
 lbfe_status lbfe_step(lbfe_handle *h, long long nsteps) {
     if (!h || nsteps < 0) return LBFE_ERR_BAD_PARAM;
     for (int k = 0; k < h->n; ++k)
         if (!h->ready[k]) return LBFE_ERR_STATE;
+    // runs of several steps replay captured graphs (no per-launch argument
+    // marshalling); inside a caller's own stream capture, or for a single
+    // step, the kernels are launched directly
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(h->stream, &cs));
+    const bool graphs = nsteps >= 2 && cs == cudaStreamCaptureStatusNone;
     const lbfe::LaunchCtx c = h->ctx();
     for (long long t = 0; t < nsteps; ++t) {
-        CK(lbfe::launch_fused(c, h->cur));
+        if (graphs) {
+            if (!h->step_graph[h->cur]) CK(build_step_graph(h, h->cur));
+            CK(cudaGraphLaunch(h->step_graph[h->cur], h->stream));
+        } else {
+            CK(lbfe::launch_fused(c, h->cur));
+        }
         h->cur ^= 1;
     }
     for (int k = 0; k < h->n; ++k) h->steps[k] += nsteps;
@@ -665,6 +708,8 @@ lbfe_status lbfe_launch_config(const lbfe_handle *h, int *step_kernel, int *tile
 lbfe_status lbfe_destroy(lbfe_handle *h) {
     if (!h) return LBFE_ERR_BAD_PARAM;
     cudaStreamSynchronize(h->stream);
+    h->drop_graphs();
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
     return LBFE_OK;
 }
