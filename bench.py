@@ -163,9 +163,14 @@ STEP_SOURCES = ("lbfe_internal.cuh", "lbfe_step.cuh", "lbfe_fused.cu", "lbfe_fus
 
 
 def kernel_source_hash():
+    """Hash of the step-kernel sources with comments and layout removed, so
+    that a profile summary survives edits to comments only."""
     h = hashlib.sha256()
     for fn in STEP_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_1411_2181_gb300", "csrc", fn), "rb").read())
+        src = open(os.path.join(ROOT, "paper_1411_2181_gb300", "csrc", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update(re.sub(r"\s+", " ", src).strip().encode())
     return h.hexdigest()[:16]
 
 

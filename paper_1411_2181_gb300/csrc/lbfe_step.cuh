@@ -3,15 +3,15 @@
 // per thread): launch descriptors, TMEM / TMA / mbarrier access, the
 // shared-memory rings and the per-cell stage functions.
 //
-// One time step of the hybrid LBM / FENE-P method (Sec. 2)
-// in a single persistent kernel that reads every population and conformation
-// component once and writes it once.
+// One time step of the hybrid LBM / FENE-P method (Sec. 2) runs as a single
+// persistent kernel that reads every population and conformation component
+// once and writes it once.
 //
 // Work decomposition.  A work item is a column tile of 32 x TY cells in the
-// x-y plane over a chunk [z0, z1) of planes of one instance; blocks stride
-// over the work items of all instances of a batch.  Inside an item the block
-// marches along z with shared-memory rings holding, per plane, the fields the
-// stencils need:
+// x-y plane over a chunk [z0, z1) of planes of one instance.  Block b starts
+// with item b; launches with more items than blocks hand out the rest from
+// a counter.  Inside an item the block marches along z with shared-memory
+// rings holding, per plane, the fields the stencils need:
 //   stage M(p)    moments rho_A, rho_B, j and the polymer stress
 //                 Pi = (eta_P/tau_P) chi (f C - I) of plane p on the
 //                 radius-2 region (36 x (TY+4) cells; the halo is recomputed
@@ -33,19 +33,22 @@
 // rho, C and Pi); the velocity ghost 2 U_wall - u is applied in stage U.
 //
 // Blackwell specifics.
-//  * The tile's own 32 x TY populations of the next plane arrive by one TMA
-//    tensor copy (box 32 x TY x 1 x 38 of the (x, y, z, population) view)
-//    into a shared-memory staging buffer, issued as soon as stage M has
-//    consumed the buffer: the DRAM reads of plane p+1 overlap stages F, X
-//    and U of plane p.  Completion is tracked by an mbarrier with a bounded
-//    wait.  The radius-2 halo (recomputed) and ragged-tile cells are read
-//    with ordinary loads.
-//  * Each thread's own-cell populations, decoded to FP32 in stage M(p), wait
-//    in tensor memory (TMEM) for the collision X(p) one plane later: two
-//    plane buffers of 38 columns per warp in the warp's 32-lane quarter,
-//    written and read with tcgen05.st / tcgen05.ld.  The collision therefore
-//    issues no global loads, and the register file does not hold the
-//    populations across the stencil stages.
+//  * TMA staging: one elected thread copies the next plane into a shared
+//    staging buffer as soon as stage M has consumed it, so the DRAM reads of
+//    plane p+1 overlap stages F, X and U of plane p; completion is tracked by
+//    an mbarrier with a bounded wait.  Tiles of up to 12 rows copy their
+//    whole radius-2 region (populations and conformation, two boxes); tiles
+//    of 16 rows copy their own cells and read the halo with ordinary loads.
+//    Cells across a periodic seam and ragged-tile cells use ordinary loads
+//    (through L2 only: the large shared carve-out leaves little L1).
+//  * TMEM handoff: each thread's own-cell populations, decoded to FP32 in
+//    stage M(p), wait in tensor memory for the collision X(p) one plane
+//    later (two plane buffers of 38 columns per warp in its 32-lane quarter,
+//    tcgen05.st / tcgen05.ld); the collision issues no global loads and the
+//    register file does not carry the populations through the stencil
+//    stages.  At 8 rows the loads back are issued before stage F.
+//  * Packed FP32: both components travel as (A, B) pairs through the moment
+//    sums and the collision (two FP32 lanes per instruction).
 //  * The instance descriptors travel in the kernel parameter space (up to
 //    64 instances per launch): scalars and pointers come from the constant
 //    bank instead of per-use global loads.
