@@ -80,7 +80,7 @@ lbfe_status derive(const lbfe_params &p, Derived &d) {
 }
 
 struct Layout {
-    size_t inst_off, tile_off, item_off, status_off, mass_off;
+    size_t inst_off, tile_off, item_off, status_off, mass_off, maps_off;
     std::vector<size_t> f_off[2], C_off[2], scratch_off, prof_off, mpart_off, dens_off;
     size_t total;
 };
@@ -99,6 +99,7 @@ Layout plan(const lbfe_params *p, int n) {
     L.item_off = take(sizeof(int) * (size_t)(n + 1));
     L.status_off = take(sizeof(unsigned) * (4 + (size_t)n));  // launch word, then one per instance
     L.mass_off = take(sizeof(double) * 2);
+    L.maps_off = take(sizeof(lbfe::StepMaps) * 2 * (size_t)n);   // TMA maps, [instance][parity]
     const size_t eb = elem_bytes(p[0].precision);
     for (int k = 0; k < n; ++k) {
         const size_t S = (size_t)stride_of(p[k]);
@@ -215,6 +216,7 @@ struct lbfe_handle {
     int *item_off = nullptr;
     std::vector<int> item_off_h;
     std::vector<lbfe::PopMaps> maps;
+    lbfe::StepMaps *maps_dev = nullptr;
     int total_items = 0, fused_grid = 0, tile_y = 16, z_chunk_req = 0, num_sms = 0, blocks_per_sm = 0;
     int step_kernel = LBFE_STEP_CELL;
     unsigned *status = nullptr;
@@ -247,6 +249,7 @@ struct lbfe_handle {
         c.item_off = item_off;
         c.item_off_host = item_off_h.data();
         c.maps_host = maps.empty() ? nullptr : maps.data();
+        c.maps_dev = maps_dev;
         c.fused_slots = num_sms * blocks_per_sm;
         c.total_items = total_items;
         c.fused_grid = fused_grid;
@@ -305,10 +308,16 @@ static lbfe_status configure_fused(lbfe_handle *h, int step_kernel, int tile_y, 
     h->total_items = off[h->n];
     h->item_off_h = off;
     h->maps.assign(h->n, lbfe::PopMaps{});
+    std::vector<lbfe::StepMaps> md(2 * (size_t)h->n);
     for (int k = 0; k < h->n; ++k) {
         e = lbfe::fused_pop_maps(h->inst[k], h->precision, tile_y, &h->maps[k]);
         if (e != cudaSuccess) return cuda_fail(e, "fused_pop_maps");
+        md[2 * k] = h->maps[k].m[0];
+        md[2 * k + 1] = h->maps[k].m[1];
     }
+    e = cudaMemcpyAsync(h->maps_dev, md.data(), sizeof(lbfe::StepMaps) * md.size(), cudaMemcpyHostToDevice,
+                        h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "configure_fused");
     h->fused_grid = (int)std::min<long long>(h->total_items, slots);
     e = cudaMemcpyAsync(h->inst_dev, h->inst.data(), sizeof(InstDev) * h->n, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->item_off, off.data(), sizeof(int) * (h->n + 1), cudaMemcpyHostToDevice, h->stream);
@@ -393,6 +402,7 @@ lbfe_status lbfe_create(lbfe_handle **hp, const lbfe_params *p, int n, void *dev
     h->item_off = (int *)(h->base + L.item_off);
     h->status = (unsigned *)(h->base + L.status_off);
     h->mass = (double *)(h->base + L.mass_off);
+    h->maps_dev = (lbfe::StepMaps *)(h->base + L.maps_off);
     std::vector<int> toff(n + 1, 0);
     int maxLx = 0;
     for (int k = 0; k < n; ++k) {

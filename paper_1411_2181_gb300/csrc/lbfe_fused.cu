@@ -25,21 +25,23 @@ k_fused(const __grid_constant__ StepArgs A) {
     __shared__ u32 s_rows[RY];   // in-plane offsets of the radius-2 rows (wrapped)
     __shared__ u32 s_cols[RX];   // x of the radius-2 columns (wrapped)
     __shared__ u32 s_tmem;       // TMEM base address of the block
-    __shared__ __align__(8) unsigned long long s_bar;   // TMA completion barrier
+    __shared__ __align__(8) unsigned long long s_bar[2];   // TMA completion barriers, one per staging buffer
 
     const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
     const int idx_in = (ty + 2) * RX + (tx + 2);
     // staging buffer for the TMA boxes: after the rings, 128-byte aligned
     const u32 smem_base = smem_addr(lbfe_smem4);
     const u32 stage_addr = (smem_base + (u32)(sizeof(float) * Gm::FLOATS) + 127u) & ~127u;
-    const T *stage = reinterpret_cast<const T *>(reinterpret_cast<const char *>(lbfe_smem4) + (stage_addr - smem_base));
-    const float *stage_c = reinterpret_cast<const float *>(reinterpret_cast<const char *>(stage) + St::C_OFF);
-    const u32 bar = smem_addr(&s_bar);
-    u32 parity = 0;
+    const char *stage0 = reinterpret_cast<const char *>(lbfe_smem4) + (stage_addr - smem_base);
+    u32 jj = 0;                      // stage-M iterations so far; buffer jj % NBUF
+    u32 ph[2] = {0u, 0u};            // completed phases waited for, per buffer
     bool waits_ok = true;
 
     if (ty == 0) tm_alloc(&s_tmem, Gm::TMEM_COLS);
-    if (t == 0) mbar_init(bar);
+    if (t == 0) {
+        mbar_init(smem_addr(&s_bar[0]));
+        mbar_init(smem_addr(&s_bar[1]));
+    }
     tm_fence_before();
     __syncthreads();
     tm_fence_after();
@@ -58,7 +60,10 @@ k_fused(const __grid_constant__ StepArgs A) {
         // the first plane of the block's first item
         if (first < A.total_items) {
             const ItemPos P0 = item_pos<TY>(A, first);
-            if (A.inst[P0.k].tma) issue_plane<T, TY>(A, P0, P0.z0 - 2, stage_addr, bar);
+            // the first NBUF planes (an item has at least five)
+            if (A.inst[P0.k].tma)
+                for (int b = 0; b < St::NBUF; ++b)
+                    issue_plane<T, TY>(A, P0, P0.z0 - 2 + b, stage_addr + b * St::BUF, smem_addr(&s_bar[b]));
         }
     }
     __syncthreads();
@@ -136,6 +141,10 @@ k_fused(const __grid_constant__ StepArgs A) {
             L.cu[2] = L.cf[1];
             L.j3 = ring2(q);
 
+            // staging buffer of this plane
+            const int sb = St::NBUF > 1 ? (int)(jj % St::NBUF) : 0;
+            const T *stage = reinterpret_cast<const T *>(stage0 + sb * St::BUF);
+            const float *stage_c = reinterpret_cast<const float *>(stage0 + sb * St::BUF + St::C_OFF);
             // ---------------- stage M(p): radius-2 region of plane clamp(p)
             {
                 const u32 pl = (u32)(min(max(p, 0), Lz - 1) * LxLy);
@@ -155,8 +164,8 @@ k_fused(const __grid_constant__ StepArgs A) {
                         }
                 }
                 if (tma) {
-                    waits_ok &= mbar_wait(bar, parity);
-                    parity ^= 1u;
+                    waits_ok &= mbar_wait(smem_addr(&s_bar[sb]), ph[sb] & 1u);
+                    ++ph[sb];
                 }
                 {
                     // own cell; its populations wait in TMEM for stage X(p)
@@ -183,18 +192,21 @@ k_fused(const __grid_constant__ StepArgs A) {
                 }
             }
             __syncthreads();
-            // the staging buffer is free: start the copy of the next plane
-            // (of this item, else of the block's next item)
+            // the staging buffer is free: start the copy of the plane NBUF
+            // ahead (of this item, else of the block's next item)
             if (t == 0) {
                 if (p == z0 - 2) s_item[slot ^ 1] = next_t0;
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                if (p < z1 + 1) {
-                    if (tma) issue_plane<T, TY>(A, P, p + 1, stage_addr, bar);
+                const u32 dst = stage_addr + sb * St::BUF, bar = smem_addr(&s_bar[sb]);
+                const int pa = p + St::NBUF;
+                if (pa <= z1 + 1) {
+                    if (tma) issue_plane<T, TY>(A, P, pa, dst, bar);
                 } else if (next_t0 < A.total_items) {
                     const ItemPos Pn = item_pos<TY>(A, next_t0);
-                    if (A.inst[Pn.k].tma) issue_plane<T, TY>(A, Pn, Pn.z0 - 2, stage_addr, bar);
+                    if (A.inst[Pn.k].tma) issue_plane<T, TY>(A, Pn, Pn.z0 - 2 + (pa - (z1 + 2)), dst, bar);
                 }
             }
+            ++jj;
             // the collision's populations start to come back from TMEM here (or
             // just before the collision) and are waited for after stage F
             const bool doX = q >= z0 && q < z1;
@@ -277,7 +289,7 @@ k_fused(const __grid_constant__ StepArgs A) {
     if (t == 0 && A.total_items > (int)gridDim.x) release_work_counters(A.work);
     if (!waits_ok) {
         // a copy may still be in flight: give it one more bounded wait
-        mbar_wait(bar, parity);
+        for (int b = 0; b < St::NBUF; ++b) mbar_wait(smem_addr(&s_bar[b]), ph[b] & 1u);
         if (t == 0) atomicOr(A.status, kFlagTimeout);
     }
     tm_fence_before();
@@ -289,11 +301,10 @@ k_fused(const __grid_constant__ StepArgs A) {
 // ---------------------------------------------------------------- host side
 namespace {
 
-void fill_inst(StepInst &d, const InstDev &I, const PopMaps *maps, int cur) {
+void fill_inst(StepInst &d, const InstDev &I, const PopMaps *maps, const StepMaps *maps_dev, int cur) {
     d = StepInst{};
-    if (maps && maps->ok) {
-        d.pop_map = maps->f[cur];
-        d.c_map = maps->c[cur];
+    if (maps && maps->ok && maps_dev) {
+        d.maps = maps_dev + cur;
         d.tma = 1;
     }
     d.Lx = (unsigned short)I.Lx;
@@ -396,7 +407,8 @@ cudaError_t fused_group(const LaunchCtx &c, int cur, int k0, int k1) {
     const int base = c.item_off_host[k0];
     for (int k = k0; k < k1; ++k) {
         a.item_off[k - k0] = c.item_off_host[k] - base;
-        fill_inst(a.inst[k - k0], c.inst_host[k], c.maps_host ? c.maps_host + k : nullptr, cur);
+        fill_inst(a.inst[k - k0], c.inst_host[k], c.maps_host ? c.maps_host + k : nullptr,
+                  c.maps_dev ? c.maps_dev + 2 * k : nullptr, cur);
     }
     a.item_off[a.n] = c.item_off_host[k1] - base;
     a.total_items = a.item_off[a.n];
@@ -436,11 +448,11 @@ cudaError_t launch_fused(const LaunchCtx &c, int cur) {
 int fused_launches(int n) { return n <= 1 ? 1 : (n + kStepMaxInst - 1) / kStepMaxInst; }
 
 // The populations of an instance viewed as a 4-D tensor (x, y, z, s*19 + i)
-// with strides (1, Lx, Lx Ly, S) elements, and the conformation as
-// (x, y, z, component).  Tiles of 16 rows copy their own 32 x 16 cells;
-// lower tiles copy the radius-2 region (boxes as in Stage).  TMA needs
-// every stride to be a multiple of 16 bytes, so instances with
-// Lx * element size not divisible by 16 keep ordinary loads.
+// with strides (1, Lx, Lx Ly, S) elements, the conformation as
+// (x, y, z, component) and the offset densities as (x, y, z) of 8-byte
+// float2; boxes as in Stage.  TMA needs every stride to be a multiple of
+// 16 bytes, so instances with Lx * element size not divisible by 16 keep
+// ordinary loads.
 cudaError_t fused_pop_maps(const InstDev &I, int precision, int tile_y, PopMaps *m) {
     std::memset(m, 0, sizeof *m);
     const size_t esz = precision == LBFE_FP32 ? 4 : 2;
@@ -451,23 +463,30 @@ cudaError_t fused_pop_maps(const InstDev &I, int precision, int tile_y, PopMaps 
                                    : precision == LBFE_BF16_OFFSET ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                                    : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     const bool region = tile_y <= 12;
-    const cuuint32_t xpad = (cuuint32_t)(16 / esz);
+    const cuuint32_t xpad = (cuuint32_t)(16 / esz), ty = (cuuint32_t)tile_y;
     const cuuint64_t dims[4] = {(cuuint64_t)I.Lx, (cuuint64_t)I.Ly, (cuuint64_t)I.Lz, (cuuint64_t)(2 * Q)};
     const cuuint64_t strides[3] = {(cuuint64_t)I.Lx * esz, (cuuint64_t)I.Lx * I.Ly * esz, (cuuint64_t)I.S * esz};
-    const cuuint32_t box[4] = {region ? 32u + 2 * xpad : 32u, (cuuint32_t)(region ? tile_y + 4 : tile_y), 1u,
-                               (cuuint32_t)(2 * Q)};
+    const cuuint32_t box[4] = {region ? 32u + 2 * xpad : 32u, region ? ty + 4 : ty, 1u, (cuuint32_t)(2 * Q)};
     const cuuint64_t cdims[4] = {(cuuint64_t)I.Lx, (cuuint64_t)I.Ly, (cuuint64_t)I.Lz, 6};
     const cuuint64_t cstrides[3] = {(cuuint64_t)I.Lx * 4, (cuuint64_t)I.Lx * I.Ly * 4, (cuuint64_t)I.S * 4};
-    const cuuint32_t cbox[4] = {40u, (cuuint32_t)(tile_y + 4), 1u, 6u};
+    const cuuint32_t cbox[4] = {40u, ty + 4, 1u, 6u};
+    const cuuint64_t ddims[3] = {(cuuint64_t)I.Lx, (cuuint64_t)I.Ly, (cuuint64_t)I.Lz};
+    const cuuint64_t dstrides[2] = {(cuuint64_t)I.Lx * 8, (cuuint64_t)I.Lx * I.Ly * 8};
+    const cuuint32_t dbox[3] = {36u, ty + 4, 1u};
     const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+    auto enc = [&](CUtensorMap *map, CUtensorMapDataType t, cuuint32_t rank, void *base, const cuuint64_t *d,
+                   const cuuint64_t *st, const cuuint32_t *bx) {
+        return fn(map, t, rank, base, d, st, bx, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    };
     for (int b = 0; b < 2; ++b) {
-        CUresult r = fn(&m->f[b], dt, 4, I.f[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        StepMaps &sm = m->m[b];
+        CUresult r = enc(&sm.pop, dt, 4, I.f[b], dims, strides, box);
         if (r == CUDA_SUCCESS && region)
-            r = fn(&m->c[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, I.C[b], cdims, cstrides, cbox, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            r = enc(&sm.c, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, I.C[b], cdims, cstrides, cbox);
+        // the state in f[b] is stored relative to dens[b ^ 1]
+        if (r == CUDA_SUCCESS && region && esz == 2 && I.dens[b ^ 1])
+            r = enc(&sm.dens, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, I.dens[b ^ 1], ddims, dstrides, dbox);
         if (r != CUDA_SUCCESS) {
             std::memset(m, 0, sizeof *m);
             return cudaSuccess;

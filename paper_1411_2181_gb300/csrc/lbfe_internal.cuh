@@ -148,13 +148,21 @@ struct LaunchCtx {
     int step_kernel;                 // lbfe_step_kernel
     int fused_slots;                 // resident blocks of the fused kernel on the GPU
     const struct PopMaps *maps_host; // per instance: TMA maps of the step kernel (may be null)
+    const struct StepMaps *maps_dev; // device copies, [instance][parity]
 };
-// Tensor maps of the step kernel's own-tile TMA loads, one per population
-// buffer f[0], f[1] of an instance; ok = 0 when the instance's layout does
-// not allow them (the kernel then reads those cells with ordinary loads).
+// Tensor maps of the step kernels' TMA copies for one parity of the
+// ping-pong state: populations f[b], conformation C[b] and the offset
+// densities of the state read (reduced forms).  They live in global memory
+// (the handle's block); the launch descriptor points at them.
+struct StepMaps {
+    CUtensorMap pop;    // box of the tile's own cells (16 rows) or of its radius-2 region (8, 12 rows)
+    CUtensorMap c;      // conformation, region box
+    CUtensorMap dens;   // offset densities (float2 per cell), region box
+};
+// Both parities of an instance; ok = 0 when the instance's layout does not
+// allow TMA (the kernel then reads with ordinary loads).
 struct PopMaps {
-    CUtensorMap f[2];   // populations f[0], f[1]
-    CUtensorMap c[2];   // conformation C[0], C[1] (region copies)
+    StepMaps m[2];
     int ok;
 };
 cudaError_t fused_pop_maps(const InstDev &I, int precision, int tile_y, PopMaps *m);

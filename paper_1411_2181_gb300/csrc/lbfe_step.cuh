@@ -67,9 +67,7 @@ constexpr int kStepMaxInst = 64;
 
 // Per-instance descriptor of one launch (kernel parameter space).
 struct StepInst {
-    CUtensorMap pop_map;           // (x, y, z, population) view of fin (when tma): box of the tile's
-                                   // own 32 x TY cells (TY = 16), or of its radius-2 region (TY <= 12)
-    CUtensorMap c_map;             // (x, y, z, component) view of Cin, region box (TY <= 12)
+    const StepMaps *maps;          // TMA maps of fin, Cin and dens_in in global memory (when tma)
     const void *fin;               // populations read (state t)
     void *fout;                    // populations written (state t + 1)
     const float *Cin;
@@ -83,7 +81,7 @@ struct StepInst {
     signed char visc_comp;         // 0 (A), 1 (B), -1 Newtonian
     signed char tma;               // populations (and C) by TMA
 };
-static_assert(sizeof(StepInst) == 384, "two tensor maps and 128 bytes of scalars");
+static_assert(sizeof(StepInst) <= 144, "compact launch descriptor");
 
 // One launch covers up to kStepMaxInst instances.  A single instance takes
 // the same kernel as a batch, so that batching never changes the arithmetic
@@ -160,6 +158,13 @@ __device__ __forceinline__ void mbar_expect(u32 bar, u32 bytes) {
 // One thread: start the copy of the box at (x, y, z, 0) into shared memory at
 // dst, completing on the barrier.  x may be negative (out-of-range elements
 // read as zero) but x * element size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_box3(const CUtensorMap *map, u32 dst, u32 bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
 __device__ __forceinline__ void tma_box4(const CUtensorMap *map, u32 dst, u32 bar, int x, int y, int z) {
     asm volatile(
         "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
@@ -331,7 +336,16 @@ struct Stage {
     static constexpr u32 C_OFF = (POP_BYTES + 127u) & ~127u;
     static constexpr int C_PLANE = 40 * BH;              // floats between components
     static constexpr u32 C_BYTES = REGION ? (u32)(C_PLANE * 6 * sizeof(float)) : 0u;
-    static constexpr u32 BYTES = C_OFF + C_BYTES;
+    // offset densities of the reduced forms, 36 x BH float2 from 2 cells left
+    static constexpr bool DENS = REGION && sizeof(T) == 2;
+    static constexpr u32 D_OFF = (C_OFF + C_BYTES + 127u) & ~127u;
+    static constexpr u32 D_BYTES = DENS ? (u32)(36 * BH * sizeof(float2)) : 0u;
+    static constexpr u32 BUF = (D_OFF + D_BYTES + 127u) & ~127u;   // one staging buffer
+    // staging buffers (copies run NBUF planes ahead).  A second buffer fits
+    // 8-row tiles with 2-byte storage but measured slower (8.3 vs 9.2 G
+    // lattice updates/s on 192 x 96 x 80), so every shape uses one.
+    static constexpr int NBUF = 1;
+    static constexpr u32 BYTES = NBUF * BUF;
 };
 
 extern __shared__ float4 lbfe_smem4[];
@@ -399,7 +413,14 @@ template <typename T, int TY>
 __device__ __forceinline__ void m_load_region(const StepInst &I, const T *sp, const float *sc, int gx, int gy, u32 n,
                                               MCell &m) {
     using St = Stage<T, TY>;
-    const float2 o = cell_offsets<T>(I, n);
+    // offset densities: staged with the region when tracked per cell
+    float2 o = make_float2(0.f, 0.f);
+    if (Store<T>::offset) {
+        if (St::DENS && I.dens_in)
+            o = reinterpret_cast<const float2 *>(reinterpret_cast<const char *>(sp) + St::D_OFF)[gy * 36 + gx];
+        else
+            o = cell_offsets<T>(I, n);
+    }
     const int e = gy * St::BW + gx - 2 + St::XPAD;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -722,12 +743,14 @@ __device__ __forceinline__ void issue_plane(const StepArgs &A, const ItemPos &P,
     const StepInst &I = A.inst[P.k];
     const int z = min(max(plane, 0), I.Lz - 1);
     if (St::REGION) {
-        mbar_expect(bar, St::POP_BYTES + St::C_BYTES);
-        tma_box4(&I.pop_map, dst, bar, P.bx * 32 - St::XPAD, P.by * TY - 2, z);
-        tma_box4(&I.c_map, dst + St::C_OFF, bar, P.bx * 32 - 4, P.by * TY - 2, z);
+        const bool dcopy = St::DENS && I.dens_in != nullptr;   // offset densities tracked per cell
+        mbar_expect(bar, St::POP_BYTES + St::C_BYTES + (dcopy ? St::D_BYTES : 0u));
+        tma_box4(&I.maps->pop, dst, bar, P.bx * 32 - St::XPAD, P.by * TY - 2, z);
+        tma_box4(&I.maps->c, dst + St::C_OFF, bar, P.bx * 32 - 4, P.by * TY - 2, z);
+        if (dcopy) tma_box3(&I.maps->dens, dst + St::D_OFF, bar, P.bx * 32 - 2, P.by * TY - 2, z);
     } else {
         mbar_expect(bar, St::POP_BYTES);
-        tma_box4(&I.pop_map, dst, bar, P.bx * 32, P.by * TY, z);
+        tma_box4(&I.maps->pop, dst, bar, P.bx * 32, P.by * TY, z);
     }
 }
 

@@ -56,3 +56,23 @@ def test_reduced_storage_errors(runs, prec, tol_D, tol_theta, tol_mass):
     dm = max((np.abs(np.array(r["mass"]) - m0) / m0).max() for r in red)
     print(f"precision {prec}: max |dD| {dD:.2e}, max |dtheta| {dth:.3f} deg, mass drift {dm:.2e}")
     assert dD < tol_D and dth < tol_theta and dm < tol_mass
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_reduced_storage_launch_shapes_agree(L, prec):
+    """The reduced storage forms give the same fields, to a few storage ulps,
+    at every launch shape: 8-row tiles (region copies, double-buffered),
+    16-row tiles (own-cell copies) and two cells per thread."""
+    p0, rho, _ = configs.config3(crop=True)
+    p = replace(p0, precision=prec)
+    out = []
+    for kernel, ty in ((0, 8), (0, 16), (1, 16)):
+        s = L.Solver(p)
+        s.tune(ty, 0, kernel)
+        s.init(0, rho)
+        s.step(40)
+        out.append(s.get_field(0, L.FIELD_F))
+    ref = out[0]
+    scale = np.abs(ref).max()
+    for f in out[1:]:
+        assert np.abs(f - ref).max() <= (2e-3 if prec == 1 else 2e-2) * scale
