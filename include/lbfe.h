@@ -167,7 +167,10 @@ lbfe_status lbfe_step(lbfe_handle *h, long long nsteps);
 /* Observables of instance k (synchronises the stream). */
 lbfe_status lbfe_observables(lbfe_handle *h, int k, lbfe_obs *out);
 
-/* DIVERGED if any instance has flagged a blow-up, else OK (synchronises). */
+/* TIMEOUT if a bounded device-side wait of the step kernel expired (a TMA
+ * copy that did not complete in time; the kernel finishes without it and
+ * the step's result is invalid), else DIVERGED if any instance has flagged a
+ * blow-up, else OK (synchronises). */
 lbfe_status lbfe_check(lbfe_handle *h);
 
 /* Copy a field of instance k to / from host memory (float32; bytes must be

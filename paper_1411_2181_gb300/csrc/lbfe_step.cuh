@@ -37,7 +37,8 @@
 //    staging buffer as soon as stage M has consumed it, so the DRAM reads of
 //    plane p+1 overlap stages F, X and U of plane p; completion is tracked by
 //    an mbarrier with a bounded wait.  Tiles of up to 12 rows copy their
-//    whole radius-2 region (populations and conformation, two boxes); tiles
+//    whole radius-2 region (populations, conformation and, in the reduced
+//    storage forms, the offset densities: one box each); tiles
 //    of 16 rows copy their own cells and read the halo with ordinary loads.
 //    Cells across a periodic seam and ragged-tile cells use ordinary loads
 //    (through L2 only: the large shared carve-out leaves little L1).

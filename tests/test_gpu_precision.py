@@ -61,7 +61,7 @@ def test_reduced_storage_errors(runs, prec, tol_D, tol_theta, tol_mass):
 @pytest.mark.parametrize("prec", [1, 2])
 def test_reduced_storage_launch_shapes_agree(L, prec):
     """The reduced storage forms give the same fields, to a few storage ulps,
-    at every launch shape: 8-row tiles (region copies, double-buffered),
+    at every launch shape: 8-row tiles (copies of the radius-2 region),
     16-row tiles (own-cell copies) and two cells per thread."""
     p0, rho, _ = configs.config3(crop=True)
     p = replace(p0, precision=prec)
