@@ -10,8 +10,9 @@ DV: eta_P = beta lambda eta_M (eta_P/eta_d = beta); MV: eta_P = beta eta_M.
 
 SIGMA is the interfacial tension of the Shan-Chen coupling G = 3.1 with
 rho_in = 1, rho_out = 0.04, fitted from the Laplace law p_in - p_out = sigma/R
-of static cylindrical droplets (R = 8..16) in the CPU oracle.  It only
-enters the bookkeeping of Ca, De and tau_em.
+of static cylindrical droplets (R = 8..16) in the CPU oracle (recipe and
+value recorded in tests/golden/shan_chen_constants.txt).  It only enters
+the bookkeeping of Ca, De and tau_em.
 """
 from __future__ import annotations
 

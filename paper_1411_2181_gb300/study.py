@@ -38,7 +38,8 @@ from .params import Params
 # through the Shan-Chen miscibility, faster at high viscosity (the mutual
 # diffusivity grows with tau - 1/2); the study therefore uses a stronger
 # coupling G = 3.8 (flat-interface coexistence densities 1.05503 / 0.01288,
-# sigma = 0.0985 from the oracle's Laplace fit), droplets with 2R/W in
+# sigma = 0.0985 from the oracle's Laplace fit; both recorded in
+# tests/golden/shan_chen_constants.txt), droplets with 2R/W in
 # [0.6, 0.8] at W = 40, and varies Ca through the matrix viscosity at the
 # wall speed 0.08, which keeps every BGK relaxation time below about 11
 # (runs with tau above about 13 in the droplet diverge at this coupling).
