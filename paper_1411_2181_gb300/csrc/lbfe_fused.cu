@@ -271,8 +271,11 @@ k_fused(const __grid_constant__ StepArgs A) {
                     if (Store<T>::offset && Po.track) I.dens_out[nq] = Po.own;
                 }
             }
-            __syncthreads();  // u of plane q complete on the radius-1 region
-            // ---------------- stage U(r): FENE-P update, Eq. 2 (Eq. 4)
+            // ---------------- stage U(r): FENE-P update, Eq. 2 (Eq. 4).  It
+            // reads u of plane r on the radius-1 region (complete since the
+            // previous plane's barriers) and u of plane q of its own cell only
+            // (written above by this thread), so it needs no barrier after
+            // stage F: threads without halo work in stage F go on to it.
             if (r >= z0 && r < z1 && valid) {
                 float cn[6];
                 if (!stage_u_cell<TY>(I, idx_in, L, r, cn)) raise_step_flag(A.status, I, kFlagDiverged);
@@ -280,7 +283,7 @@ k_fused(const __grid_constant__ StepArgs A) {
 #pragma unroll
                 for (int q6 = 0; q6 < 6; ++q6) Cout[(u32)(q6 * S + n)] = cn[q6];
             }
-            __syncthreads();  // stage U done with the rings before stage M(p+1)
+            __syncthreads();  // stages F, X and U done with the rings before stage M(p+1)
         }
         item = s_item[slot ^ 1];   // published in the first iteration, several barriers ago
         slot ^= 1;

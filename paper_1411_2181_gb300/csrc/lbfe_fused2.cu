@@ -566,8 +566,8 @@ __global__ void __launch_bounds__(PNT, 1) k_fused_pair(const __grid_constant__ S
                             make_float4(rAo.x, rBo.x, rAo.y, rBo.y);
                 }
             }
-            __syncthreads();
-            // ---------------- stage U(r)
+            // ---------------- stage U(r): no barrier before it (u of plane q
+            // is read at the thread's own cells only)
             if (r >= z0 && r < z1 && valid) {
                 float c0[6], c1[6];
                 bool ok = stage_u_cell<PTY>(I, idx_in, L, r, c0);

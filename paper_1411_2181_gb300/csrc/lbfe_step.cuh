@@ -26,9 +26,12 @@
 //                 conformation ring.
 // The collision of plane p-1 needs the densities of plane p (Shan-Chen); the
 // C update of plane p-2 needs the velocity of plane p-1, hence the lags.
-// Three block barriers per plane: after stage M, after stage X (stage X
-// needs only its own cell's forces, so it runs before the barrier that
-// stage U needs) and after stage U.
+// Two block barriers per plane: after stage M, and after stage U.  Stages
+// X(p-1) and U(p-2) need, from stage F(p-1), only the thread's own cell
+// (forces and u of the collision; u of plane p-1 in the z-derivative of
+// grad u), so they follow stage F without a barrier; the x- and
+// y-derivatives of stage U use u of plane p-2, complete since the previous
+// plane.
 // Planes beyond a wall are loaded as the adjacent plane (mirror ghosts of
 // rho, C and Pi); the velocity ghost 2 U_wall - u is applied in stage U.
 //
@@ -359,8 +362,6 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 __device__ __forceinline__ float2 bc(float s) { return make_float2(s, s); }
 
-// Stage M inputs of one cell: its 38 populations (decoded to FP32) and 6
-// conformation components.
 // Stage M inputs of one cell: its populations as (component A, component B)
 // pairs (decoded to FP32) and 6 conformation components.  The pairs feed
 // packed FP32 arithmetic (two lanes per instruction) in stages M and X.
