@@ -202,6 +202,18 @@ lbfe_status lbfe_tune(lbfe_handle *h, int step_kernel, int tile_y, int z_chunk);
 lbfe_status lbfe_launch_config(const lbfe_handle *h, int *step_kernel, int *tile_y, int *z_chunk, int *grid,
                                int *items);
 
+/* Test hook for the failure path of the step kernel (no counterpart in the
+ * paper).  what = LBFE_INJECT_DROP_COPIES: the step kernel issues none of
+ * its TMA copies, so that each block's bounded wait for its first copy
+ * expires (after about one second), the block finishes its work items
+ * without waiting again, and lbfe_check reports LBFE_ERR_TIMEOUT (the
+ * launch status word keeps the flag for the life of the handle).  Only
+ * instances whose staging uses TMA (Lx * element size a multiple of 16
+ * bytes) wait.  what = 0 clears the hook.  Synchronises the stream;
+ * BAD_PARAM for unknown bits. */
+#define LBFE_INJECT_DROP_COPIES 1u
+lbfe_status lbfe_test_inject(lbfe_handle *h, unsigned what);
+
 /* Observables of a population field the caller already holds on the
  * device, computed without allocating anything.  For callers that cannot
  * allocate device memory at the point where they want diagnostics: their

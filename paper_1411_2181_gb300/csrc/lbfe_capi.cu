@@ -219,6 +219,7 @@ struct lbfe_handle {
     lbfe::StepMaps *maps_dev = nullptr;
     int total_items = 0, fused_grid = 0, tile_y = 16, z_chunk_req = 0, num_sms = 0, blocks_per_sm = 0;
     int step_kernel = LBFE_STEP_CELL;
+    unsigned inject = 0;             // lbfe_test_inject bits
     unsigned *status = nullptr;
     double *mass = nullptr;
     int cur = 0;
@@ -255,6 +256,7 @@ struct lbfe_handle {
         c.fused_grid = fused_grid;
         c.tile_y = tile_y;
         c.step_kernel = step_kernel;
+        c.step_flags = (inject & LBFE_INJECT_DROP_COPIES) ? lbfe::kStepDropCopies : 0u;
         return c;
     }
 };
@@ -698,6 +700,14 @@ lbfe_status lbfe_set_field(lbfe_handle *h, int k, int which, const void *host_sr
 }
 
 int lbfe_launches_per_step(const lbfe_handle *h) { return h ? lbfe::fused_launches(h->n) : 0; }
+
+lbfe_status lbfe_test_inject(lbfe_handle *h, unsigned what) {
+    if (!h || (what & ~(unsigned)LBFE_INJECT_DROP_COPIES)) return LBFE_ERR_BAD_PARAM;
+    CK(cudaStreamSynchronize(h->stream));
+    h->inject = what;
+    h->drop_graphs();   // captured launches carry the old flags
+    return LBFE_OK;
+}
 
 lbfe_status lbfe_tune(lbfe_handle *h, int step_kernel, int tile_y, int z_chunk) {
     if (!h) return LBFE_ERR_BAD_PARAM;

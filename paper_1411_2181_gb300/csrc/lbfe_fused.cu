@@ -25,7 +25,8 @@ k_fused(const __grid_constant__ StepArgs A) {
     __shared__ u32 s_rows[RY];   // in-plane offsets of the radius-2 rows (wrapped)
     __shared__ u32 s_cols[RX];   // x of the radius-2 columns (wrapped)
     __shared__ u32 s_tmem;       // TMEM base address of the block
-    __shared__ __align__(8) unsigned long long s_bar[2];   // TMA completion barriers, one per staging buffer
+    __shared__ __align__(8) unsigned long long s_bar;   // TMA completion barrier of the staging buffer
+    __shared__ int s_fail;       // a bounded wait expired: no further copies or waits
 
     const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
     const int idx_in = (ty + 2) * RX + (tx + 2);
@@ -33,14 +34,14 @@ k_fused(const __grid_constant__ StepArgs A) {
     const u32 smem_base = smem_addr(lbfe_smem4);
     const u32 stage_addr = (smem_base + (u32)(sizeof(float) * Gm::FLOATS) + 127u) & ~127u;
     const char *stage0 = reinterpret_cast<const char *>(lbfe_smem4) + (stage_addr - smem_base);
-    u32 jj = 0;                      // stage-M iterations so far; buffer jj % NBUF
-    u32 ph[2] = {0u, 0u};            // completed phases waited for, per buffer
-    bool waits_ok = true;
+    const u32 bar = smem_addr(&s_bar);
+    u32 parity = 0;                  // phase parity of the next copy to wait for
+    u32 issued = 0;                  // copies issued (thread 0)
 
     if (ty == 0) tm_alloc(&s_tmem, Gm::TMEM_COLS);
     if (t == 0) {
-        mbar_init(smem_addr(&s_bar[0]));
-        mbar_init(smem_addr(&s_bar[1]));
+        mbar_init(bar);
+        s_fail = 0;
     }
     tm_fence_before();
     __syncthreads();
@@ -60,10 +61,10 @@ k_fused(const __grid_constant__ StepArgs A) {
         // the first plane of the block's first item
         if (first < A.total_items) {
             const ItemPos P0 = item_pos<TY>(A, first);
-            // the first NBUF planes (an item has at least five)
-            if (A.inst[P0.k].tma)
-                for (int b = 0; b < St::NBUF; ++b)
-                    issue_plane<T, TY>(A, P0, P0.z0 - 2 + b, stage_addr + b * St::BUF, smem_addr(&s_bar[b]));
+            if (A.inst[P0.k].tma && !(A.flags & kStepDropCopies)) {
+                issue_plane<T, TY>(A, P0, P0.z0 - 2, stage_addr, bar);
+                ++issued;
+            }
         }
     }
     __syncthreads();
@@ -142,9 +143,8 @@ k_fused(const __grid_constant__ StepArgs A) {
             L.j3 = ring2(q);
 
             // staging buffer of this plane
-            const int sb = St::NBUF > 1 ? (int)(jj % St::NBUF) : 0;
-            const T *stage = reinterpret_cast<const T *>(stage0 + sb * St::BUF);
-            const float *stage_c = reinterpret_cast<const float *>(stage0 + sb * St::BUF + St::C_OFF);
+            const T *stage = reinterpret_cast<const T *>(stage0);
+            const float *stage_c = reinterpret_cast<const float *>(stage0 + St::C_OFF);
             // ---------------- stage M(p): radius-2 region of plane clamp(p)
             {
                 const u32 pl = (u32)(min(max(p, 0), Lz - 1) * LxLy);
@@ -164,8 +164,10 @@ k_fused(const __grid_constant__ StepArgs A) {
                         }
                 }
                 if (tma) {
-                    waits_ok &= mbar_wait(smem_addr(&s_bar[sb]), ph[sb] & 1u);
-                    ++ph[sb];
+                    // after an expired wait the block issues no copies and
+                    // waits for none (the step is reported as failed)
+                    if (!s_fail && !mbar_wait(bar, parity)) s_fail = 1;
+                    parity ^= 1u;
                 }
                 {
                     // own cell; its populations wait in TMEM for stage X(p)
@@ -192,21 +194,26 @@ k_fused(const __grid_constant__ StepArgs A) {
                 }
             }
             __syncthreads();
-            // the staging buffer is free: start the copy of the plane NBUF
-            // ahead (of this item, else of the block's next item)
+            // the staging buffer is free: start the copy of the next plane
+            // (of this item, else the first plane of the block's next item)
             if (t == 0) {
                 if (p == z0 - 2) s_item[slot ^ 1] = next_t0;
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                const u32 dst = stage_addr + sb * St::BUF, bar = smem_addr(&s_bar[sb]);
-                const int pa = p + St::NBUF;
-                if (pa <= z1 + 1) {
-                    if (tma) issue_plane<T, TY>(A, P, pa, dst, bar);
-                } else if (next_t0 < A.total_items) {
-                    const ItemPos Pn = item_pos<TY>(A, next_t0);
-                    if (A.inst[Pn.k].tma) issue_plane<T, TY>(A, Pn, Pn.z0 - 2 + (pa - (z1 + 2)), dst, bar);
+                if (!s_fail && !(A.flags & kStepDropCopies)) {
+                    if (p + 1 <= z1 + 1) {
+                        if (tma) {
+                            issue_plane<T, TY>(A, P, p + 1, stage_addr, bar);
+                            ++issued;
+                        }
+                    } else if (next_t0 < A.total_items) {
+                        const ItemPos Pn = item_pos<TY>(A, next_t0);
+                        if (A.inst[Pn.k].tma) {
+                            issue_plane<T, TY>(A, Pn, Pn.z0 - 2, stage_addr, bar);
+                            ++issued;
+                        }
+                    }
                 }
             }
-            ++jj;
             // the collision's populations start to come back from TMEM here (or
             // just before the collision) and are waited for after stage F
             const bool doX = q >= z0 && q < z1;
@@ -290,10 +297,12 @@ k_fused(const __grid_constant__ StepArgs A) {
     }
 
     if (t == 0 && A.total_items > (int)gridDim.x) release_work_counters(A.work);
-    if (!waits_ok) {
-        // a copy may still be in flight: give it one more bounded wait
-        for (int b = 0; b < St::NBUF; ++b) mbar_wait(smem_addr(&s_bar[b]), ph[b] & 1u);
-        if (t == 0) atomicOr(A.status, kFlagTimeout);
+    if (s_fail && t == 0) {
+        // the copy whose wait expired may still be in flight (no later copy
+        // was issued): wait for its phase once more, bounded, before the
+        // block's shared memory is released
+        if (issued > 0) mbar_wait(bar, (issued - 1u) & 1u);
+        atomicOr(A.status, kFlagTimeout);
     }
     tm_fence_before();
     __syncthreads();
@@ -405,6 +414,7 @@ cudaError_t prep_ty(int precision, int *bps) {
 cudaError_t fused_group(const LaunchCtx &c, int cur, int k0, int k1) {
     StepArgs a{};
     a.n = k1 - k0;
+    a.flags = c.step_flags;
     a.status = c.status;
     a.work = c.status + 2;
     const int base = c.item_off_host[k0];

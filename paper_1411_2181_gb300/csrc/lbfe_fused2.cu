@@ -379,6 +379,7 @@ __global__ void __launch_bounds__(PNT, 1) k_fused_pair(const __grid_constant__ S
     __shared__ u32 s_cols[RX];   // x of the radius-2 columns (wrapped)
     __shared__ u32 s_tmem;
     __shared__ __align__(8) unsigned long long s_bar;
+    __shared__ int s_fail;       // a bounded wait expired: no further copies or waits
 
     const int t = threadIdx.x, lx = t & 15, ty = t >> 4, warp = t >> 5;
     const int gx0 = 2 + 2 * lx, gy0 = 2 + ty;
@@ -388,11 +389,14 @@ __global__ void __launch_bounds__(PNT, 1) k_fused_pair(const __grid_constant__ S
     const u32 stage_addr = (smem_base + (u32)(sizeof(float) * PG::FLOATS) + 127u) & ~127u;
     const T *stage = reinterpret_cast<const T *>(reinterpret_cast<const char *>(lbfe_smem4) + (stage_addr - smem_base));
     const u32 bar = smem_addr(&s_bar);
-    u32 parity = 0;
-    bool waits_ok = true;
+    u32 parity = 0;                  // phase parity of the next copy to wait for
+    u32 issued = 0;                  // copies issued (thread 0)
 
     if (warp == 0) tm_alloc(&s_tmem, P_TMEM_COLS);
-    if (t == 0) mbar_init(bar);
+    if (t == 0) {
+        mbar_init(bar);
+        s_fail = 0;
+    }
     tm_fence_before();
     __syncthreads();
     tm_fence_after();
@@ -405,7 +409,10 @@ __global__ void __launch_bounds__(PNT, 1) k_fused_pair(const __grid_constant__ S
         s_item[0] = first;
         if (first < A.total_items) {
             const ItemPos P0 = item_pos<PTY>(A, first);
-            if (A.inst[P0.k].tma) issue_plane<T, PTY>(A, P0, P0.z0 - 2, stage_addr, bar);
+            if (A.inst[P0.k].tma && !(A.flags & kStepDropCopies)) {
+                issue_plane<T, PTY>(A, P0, P0.z0 - 2, stage_addr, bar);
+                ++issued;
+            }
         }
     }
     __syncthreads();
@@ -489,7 +496,7 @@ __global__ void __launch_bounds__(PNT, 1) k_fused_pair(const __grid_constant__ S
                     m_store2(I, m, h_idx, L.r3[2], ring2(p), L.cf[2]);
                 }
                 if (tma) {
-                    waits_ok &= mbar_wait(bar, parity);
+                    if (!s_fail && !mbar_wait(bar, parity)) s_fail = 1;
                     parity ^= 1u;
                 }
                 {
@@ -506,11 +513,18 @@ __global__ void __launch_bounds__(PNT, 1) k_fused_pair(const __grid_constant__ S
             if (t == 0) {
                 if (p == z0 - 2) s_item[slot ^ 1] = next_t0;
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                if (p < z1 + 1) {
-                    if (tma) issue_plane<T, PTY>(A, P, p + 1, stage_addr, bar);
+                if (s_fail || (A.flags & kStepDropCopies)) {
+                } else if (p < z1 + 1) {
+                    if (tma) {
+                        issue_plane<T, PTY>(A, P, p + 1, stage_addr, bar);
+                        ++issued;
+                    }
                 } else if (next_t0 < A.total_items) {
                     const ItemPos Pn = item_pos<PTY>(A, next_t0);
-                    if (A.inst[Pn.k].tma) issue_plane<T, PTY>(A, Pn, Pn.z0 - 2, stage_addr, bar);
+                    if (A.inst[Pn.k].tma) {
+                        issue_plane<T, PTY>(A, Pn, Pn.z0 - 2, stage_addr, bar);
+                        ++issued;
+                    }
                 }
             }
             // ---------------- stage F(q): the pair, then the radius-1 ring
@@ -585,9 +599,11 @@ __global__ void __launch_bounds__(PNT, 1) k_fused_pair(const __grid_constant__ S
     }
 
     if (t == 0 && A.total_items > (int)gridDim.x) release_work_counters(A.work);
-    if (!waits_ok) {
-        mbar_wait(bar, parity);
-        if (t == 0) atomicOr(A.status, kFlagTimeout);
+    if (s_fail && t == 0) {
+        // the copy whose wait expired may still be in flight: wait for its
+        // phase once more, bounded, before the shared memory is released
+        if (issued > 0) mbar_wait(bar, (issued - 1u) & 1u);
+        atomicOr(A.status, kFlagTimeout);
     }
     tm_fence_before();
     __syncthreads();

@@ -134,6 +134,9 @@ __device__ __forceinline__ float peterlin(float L2, float cxx, float cyy, float 
 constexpr unsigned kFlagDiverged = 1u;
 constexpr unsigned kFlagTimeout = 2u;    // a bounded device-side wait expired (launch status only)
 
+// Step-kernel flags (StepArgs::flags)
+constexpr unsigned kStepDropCopies = 1u;   // test hook: issue no TMA copy, so that the waits expire
+
 // Launchers (lbfe_fused.cu, lbfe_fields.cu, lbfe_obs.cu).
 struct LaunchCtx {
     const InstDev *inst_dev;         // device copy of the descriptors
@@ -146,6 +149,7 @@ struct LaunchCtx {
     const int *item_off_host;        // host copy of item_off
     int total_items, fused_grid, tile_y;
     int step_kernel;                 // lbfe_step_kernel
+    unsigned step_flags = 0;         // StepArgs::flags (test hooks)
     int fused_slots;                 // resident blocks of the fused kernel on the GPU
     const struct PopMaps *maps_host; // per instance: TMA maps of the step kernel (may be null)
     const struct StepMaps *maps_dev; // device copies, [instance][parity]

@@ -92,6 +92,7 @@ static_assert(sizeof(StepInst) <= 144, "compact launch descriptor");
 // (the results of an instance are bitwise the same alone or in a batch).
 struct StepArgs {
     int n, total_items;
+    unsigned flags;                // kStep* bits
     unsigned *status;              // status word of the launch
     unsigned *work;                // [0] work-item counter, [1] finished blocks; zero between launches
     int item_off[kStepMaxInst + 1];  // first work item of each instance
@@ -149,7 +150,10 @@ __device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::
 __device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // ---------------------------------------------------------------- TMA + mbarrier
-constexpr int kWaitLimit = 1 << 22;   // try_wait rounds before a wait is declared expired
+// A wait on a copy expires after kWaitNs of GPU time (%globaltimer, read
+// every 256 rounds) or kWaitRounds try_wait rounds, whichever comes first.
+constexpr unsigned long long kWaitNs = 1000000000ull;
+constexpr u32 kWaitRounds = 1u << 24;
 
 __device__ __forceinline__ void mbar_init(u32 bar) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
@@ -176,9 +180,15 @@ __device__ __forceinline__ void tma_box4(const CUtensorMap *map, u32 dst, u32 ba
         "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(0), "r"(bar)
         : "memory");
 }
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 // Wait for the completion of phase `parity`; false once the limit expired.
 __device__ __forceinline__ bool mbar_wait(u32 bar, u32 parity) {
-    for (int it = 0; it < kWaitLimit; ++it) {
+    unsigned long long t0 = 0;
+    for (u32 it = 0; it < kWaitRounds; ++it) {
         u32 ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -187,6 +197,13 @@ __device__ __forceinline__ bool mbar_wait(u32 bar, u32 parity) {
             : "r"(bar), "r"(parity)
             : "memory");
         if (ok) return true;
+        if ((it & 255u) == 255u) {
+            const unsigned long long now = global_ns();
+            if (t0 == 0)
+                t0 = now;
+            else if (now - t0 > kWaitNs)
+                return false;
+        }
     }
     return false;
 }
@@ -344,12 +361,10 @@ struct Stage {
     static constexpr bool DENS = REGION && sizeof(T) == 2;
     static constexpr u32 D_OFF = (C_OFF + C_BYTES + 127u) & ~127u;
     static constexpr u32 D_BYTES = DENS ? (u32)(36 * BH * sizeof(float2)) : 0u;
-    static constexpr u32 BUF = (D_OFF + D_BYTES + 127u) & ~127u;   // one staging buffer
-    // staging buffers (copies run NBUF planes ahead).  A second buffer fits
-    // 8-row tiles with 2-byte storage but measured slower (8.3 vs 9.2 G
-    // lattice updates/s on 192 x 96 x 80), so every shape uses one.
-    static constexpr int NBUF = 1;
-    static constexpr u32 BYTES = NBUF * BUF;
+    // one staging buffer (a second one, copies two planes ahead, fits 8-row
+    // tiles with 2-byte storage but measured slower: 8.3 vs 9.2 G lattice
+    // updates/s on 192 x 96 x 80)
+    static constexpr u32 BYTES = (D_OFF + D_BYTES + 127u) & ~127u;
 };
 
 extern __shared__ float4 lbfe_smem4[];

@@ -25,6 +25,7 @@ _lib = ct.CDLL(LIB_PATH)
 
 FIELD_F, FIELD_C, FIELD_RHO, FIELD_U = 0, 1, 2, 3
 STEP_CELL, STEP_PAIR = 0, 1   # lbfe_step_kernel
+INJECT_DROP_COPIES = 1        # lbfe_test_inject
 
 OK, ERR_BAD_PARAM, ERR_NO_MEMORY, ERR_CUDA, ERR_DIVERGED, ERR_TIMEOUT, ERR_STATE = range(7)
 
@@ -74,6 +75,8 @@ _lib.lbfe_tune.argtypes = [_H, ct.c_int, ct.c_int, ct.c_int]
 _lib.lbfe_tune.restype = ct.c_int
 _lib.lbfe_launch_config.argtypes = [_H] + [ct.POINTER(ct.c_int)] * 5
 _lib.lbfe_launch_config.restype = ct.c_int
+_lib.lbfe_test_inject.argtypes = [_H, ct.c_uint]
+_lib.lbfe_test_inject.restype = ct.c_int
 _lib.lbfe_observables_noalloc.argtypes = [_P, ct.c_void_p, ct.c_longlong, ct.POINTER(CObs), ct.c_void_p]
 _lib.lbfe_observables_noalloc.restype = ct.c_int
 for _fn in ("lbfe_derive", "lbfe_required_bytes", "lbfe_create", "lbfe_init", "lbfe_step",
@@ -204,6 +207,10 @@ class Solver:
 
     def check(self) -> int:
         return _lib.lbfe_check(self._h)
+
+    def test_inject(self, what: int):
+        """Test hook of the step kernel's failure path (lbfe_test_inject)."""
+        _check(_lib.lbfe_test_inject(self._h, int(what)), "lbfe_test_inject")
 
     def _shape(self, k, which):
         p = self.params[k]

@@ -79,3 +79,7 @@ def test_create_rejects_small_or_misaligned_block(lbfe):
     assert lbfe._lib.lbfe_create(ct.byref(h), arr, 1, ct.c_void_p(4096), need - 1, None) == lbfe.ERR_NO_MEMORY
     assert lbfe._lib.lbfe_create(ct.byref(h), arr, 1, ct.c_void_p(4096 + 8), need, None) == lbfe.ERR_BAD_PARAM
     assert lbfe._lib.lbfe_create(ct.byref(h), arr, 0, ct.c_void_p(4096), need, None) == lbfe.ERR_BAD_PARAM
+
+
+def test_test_inject_rejects_null_handle(lbfe):
+    assert lbfe._lib.lbfe_test_inject(None, lbfe.INJECT_DROP_COPIES) == lbfe.ERR_BAD_PARAM
