@@ -203,15 +203,17 @@ lbfe_status lbfe_launch_config(const lbfe_handle *h, int *step_kernel, int *tile
                                int *items);
 
 /* Test hook for the failure path of the step kernel (no counterpart in the
- * paper).  what = LBFE_INJECT_DROP_COPIES: the step kernel issues none of
- * its TMA copies, so that each block's bounded wait for its first copy
- * expires (after about one second), the block finishes its work items
- * without waiting again, and lbfe_check reports LBFE_ERR_TIMEOUT (the
- * launch status word keeps the flag for the life of the handle).  Only
- * instances whose staging uses TMA (Lx * element size a multiple of 16
- * bytes) wait.  what = 0 clears the hook.  Synchronises the stream;
- * BAD_PARAM for unknown bits. */
-#define LBFE_INJECT_DROP_COPIES 1u
+ * paper).  what = LBFE_INJECT_SHORT_COPIES: the TMA tensor maps of the
+ * populations are rebuilt with boxes one row short of what the step kernel
+ * expects, so that the completion barrier of each block's first copy never
+ * completes.  The block's bounded wait expires (after about one second of
+ * GPU time), the whole block stops before issuing another copy, waits once
+ * more (bounded) for the copy's barrier, frees its tensor memory and exits;
+ * lbfe_check then reports LBFE_ERR_TIMEOUT (the launch status word keeps the
+ * flag for the life of the handle).  Only instances whose staging uses TMA
+ * (Lx * element size a multiple of 16 bytes) wait.  what = 0 restores the
+ * maps.  Synchronises the stream; BAD_PARAM for unknown bits. */
+#define LBFE_INJECT_SHORT_COPIES 1u
 lbfe_status lbfe_test_inject(lbfe_handle *h, unsigned what);
 
 /* Observables of a population field the caller already holds on the

@@ -256,7 +256,6 @@ struct lbfe_handle {
         c.fused_grid = fused_grid;
         c.tile_y = tile_y;
         c.step_kernel = step_kernel;
-        c.step_flags = (inject & LBFE_INJECT_DROP_COPIES) ? lbfe::kStepDropCopies : 0u;
         return c;
     }
 };
@@ -312,7 +311,8 @@ static lbfe_status configure_fused(lbfe_handle *h, int step_kernel, int tile_y, 
     h->maps.assign(h->n, lbfe::PopMaps{});
     std::vector<lbfe::StepMaps> md(2 * (size_t)h->n);
     for (int k = 0; k < h->n; ++k) {
-        e = lbfe::fused_pop_maps(h->inst[k], h->precision, tile_y, &h->maps[k]);
+        e = lbfe::fused_pop_maps(h->inst[k], h->precision, tile_y, (h->inject & LBFE_INJECT_SHORT_COPIES) != 0,
+                                 &h->maps[k]);
         if (e != cudaSuccess) return cuda_fail(e, "fused_pop_maps");
         md[2 * k] = h->maps[k].m[0];
         md[2 * k + 1] = h->maps[k].m[1];
@@ -702,11 +702,11 @@ lbfe_status lbfe_set_field(lbfe_handle *h, int k, int which, const void *host_sr
 int lbfe_launches_per_step(const lbfe_handle *h) { return h ? lbfe::fused_launches(h->n) : 0; }
 
 lbfe_status lbfe_test_inject(lbfe_handle *h, unsigned what) {
-    if (!h || (what & ~(unsigned)LBFE_INJECT_DROP_COPIES)) return LBFE_ERR_BAD_PARAM;
+    if (!h || (what & ~(unsigned)LBFE_INJECT_SHORT_COPIES)) return LBFE_ERR_BAD_PARAM;
     CK(cudaStreamSynchronize(h->stream));
     h->inject = what;
-    h->drop_graphs();   // captured launches carry the old flags
-    return LBFE_OK;
+    // rebuild the tensor maps of the current launch shape
+    return configure_fused(h, h->step_kernel, h->tile_y, h->z_chunk_req);
 }
 
 lbfe_status lbfe_tune(lbfe_handle *h, int step_kernel, int tile_y, int z_chunk) {

@@ -26,7 +26,6 @@ k_fused(const __grid_constant__ StepArgs A) {
     __shared__ u32 s_cols[RX];   // x of the radius-2 columns (wrapped)
     __shared__ u32 s_tmem;       // TMEM base address of the block
     __shared__ __align__(8) unsigned long long s_bar;   // TMA completion barrier of the staging buffer
-    __shared__ int s_fail;       // a bounded wait expired: no further copies or waits
 
     const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
     const int idx_in = (ty + 2) * RX + (tx + 2);
@@ -37,12 +36,12 @@ k_fused(const __grid_constant__ StepArgs A) {
     const u32 bar = smem_addr(&s_bar);
     u32 parity = 0;                  // phase parity of the next copy to wait for
     u32 issued = 0;                  // copies issued (thread 0)
+    // this thread's wait for a copy expired: it waits for no further copy,
+    // and thread 0 issues none (at most one copy stays outstanding)
+    bool expired = false;
 
     if (ty == 0) tm_alloc(&s_tmem, Gm::TMEM_COLS);
-    if (t == 0) {
-        mbar_init(bar);
-        s_fail = 0;
-    }
+    if (t == 0) mbar_init(bar);
     tm_fence_before();
     __syncthreads();
     tm_fence_after();
@@ -61,7 +60,7 @@ k_fused(const __grid_constant__ StepArgs A) {
         // the first plane of the block's first item
         if (first < A.total_items) {
             const ItemPos P0 = item_pos<TY>(A, first);
-            if (A.inst[P0.k].tma && !(A.flags & kStepDropCopies)) {
+            if (A.inst[P0.k].tma) {
                 issue_plane<T, TY>(A, P0, P0.z0 - 2, stage_addr, bar);
                 ++issued;
             }
@@ -164,9 +163,7 @@ k_fused(const __grid_constant__ StepArgs A) {
                         }
                 }
                 if (tma) {
-                    // after an expired wait the block issues no copies and
-                    // waits for none (the step is reported as failed)
-                    if (!s_fail && !mbar_wait(bar, parity)) s_fail = 1;
+                    if (!expired && !mbar_wait(bar, parity)) expired = true;
                     parity ^= 1u;
                 }
                 {
@@ -199,18 +196,17 @@ k_fused(const __grid_constant__ StepArgs A) {
             if (t == 0) {
                 if (p == z0 - 2) s_item[slot ^ 1] = next_t0;
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                if (!s_fail && !(A.flags & kStepDropCopies)) {
-                    if (p + 1 <= z1 + 1) {
-                        if (tma) {
-                            issue_plane<T, TY>(A, P, p + 1, stage_addr, bar);
-                            ++issued;
-                        }
-                    } else if (next_t0 < A.total_items) {
-                        const ItemPos Pn = item_pos<TY>(A, next_t0);
-                        if (A.inst[Pn.k].tma) {
-                            issue_plane<T, TY>(A, Pn, Pn.z0 - 2, stage_addr, bar);
-                            ++issued;
-                        }
+                const u32 go = expired ? 0u : 1u;
+                if (p + 1 <= z1 + 1) {
+                    if (tma) {
+                        issue_plane<T, TY>(A, P, p + 1, stage_addr, bar, go);
+                        issued += go;
+                    }
+                } else if (next_t0 < A.total_items) {
+                    const ItemPos Pn = item_pos<TY>(A, next_t0);
+                    if (A.inst[Pn.k].tma) {
+                        issue_plane<T, TY>(A, Pn, Pn.z0 - 2, stage_addr, bar, go);
+                        issued += go;
                     }
                 }
             }
@@ -297,13 +293,14 @@ k_fused(const __grid_constant__ StepArgs A) {
     }
 
     if (t == 0 && A.total_items > (int)gridDim.x) release_work_counters(A.work);
-    if (s_fail && t == 0) {
-        // the copy whose wait expired may still be in flight (no later copy
-        // was issued): wait for its phase once more, bounded, before the
-        // block's shared memory is released
-        if (issued > 0) mbar_wait(bar, (issued - 1u) & 1u);
+    if (expired) {
+        // thread 0: the copy whose wait expired may still be in flight (no
+        // later one was issued); wait for its phase once more, bounded,
+        // before the block's shared memory is released
+        if (t == 0 && issued > 0) mbar_wait(bar, (issued - 1u) & 1u);
         atomicOr(A.status, kFlagTimeout);
     }
+    tm_wait_st();   // no TMEM store may be pending when the columns are freed
     tm_fence_before();
     __syncthreads();
     tm_fence_after();
@@ -414,7 +411,6 @@ cudaError_t prep_ty(int precision, int *bps) {
 cudaError_t fused_group(const LaunchCtx &c, int cur, int k0, int k1) {
     StepArgs a{};
     a.n = k1 - k0;
-    a.flags = c.step_flags;
     a.status = c.status;
     a.work = c.status + 2;
     const int base = c.item_off_host[k0];
@@ -466,7 +462,7 @@ int fused_launches(int n) { return n <= 1 ? 1 : (n + kStepMaxInst - 1) / kStepMa
 // float2; boxes as in Stage.  TMA needs every stride to be a multiple of
 // 16 bytes, so instances with Lx * element size not divisible by 16 keep
 // ordinary loads.
-cudaError_t fused_pop_maps(const InstDev &I, int precision, int tile_y, PopMaps *m) {
+cudaError_t fused_pop_maps(const InstDev &I, int precision, int tile_y, bool short_box, PopMaps *m) {
     std::memset(m, 0, sizeof *m);
     const size_t esz = precision == LBFE_FP32 ? 4 : 2;
     if (((size_t)I.Lx * esz) % 16 != 0 || ((size_t)I.Lx * 4) % 16 != 0) return cudaSuccess;
@@ -479,7 +475,8 @@ cudaError_t fused_pop_maps(const InstDev &I, int precision, int tile_y, PopMaps 
     const cuuint32_t xpad = (cuuint32_t)(16 / esz), ty = (cuuint32_t)tile_y;
     const cuuint64_t dims[4] = {(cuuint64_t)I.Lx, (cuuint64_t)I.Ly, (cuuint64_t)I.Lz, (cuuint64_t)(2 * Q)};
     const cuuint64_t strides[3] = {(cuuint64_t)I.Lx * esz, (cuuint64_t)I.Lx * I.Ly * esz, (cuuint64_t)I.S * esz};
-    const cuuint32_t box[4] = {region ? 32u + 2 * xpad : 32u, region ? ty + 4 : ty, 1u, (cuuint32_t)(2 * Q)};
+    const cuuint32_t box[4] = {region ? 32u + 2 * xpad : 32u, (region ? ty + 4 : ty) - (short_box ? 1u : 0u), 1u,
+                               (cuuint32_t)(2 * Q)};
     const cuuint64_t cdims[4] = {(cuuint64_t)I.Lx, (cuuint64_t)I.Ly, (cuuint64_t)I.Lz, 6};
     const cuuint64_t cstrides[3] = {(cuuint64_t)I.Lx * 4, (cuuint64_t)I.Lx * I.Ly * 4, (cuuint64_t)I.S * 4};
     const cuuint32_t cbox[4] = {40u, ty + 4, 1u, 6u};

@@ -379,7 +379,6 @@ __global__ void __launch_bounds__(PNT, 1) k_fused_pair(const __grid_constant__ S
     __shared__ u32 s_cols[RX];   // x of the radius-2 columns (wrapped)
     __shared__ u32 s_tmem;
     __shared__ __align__(8) unsigned long long s_bar;
-    __shared__ int s_fail;       // a bounded wait expired: no further copies or waits
 
     const int t = threadIdx.x, lx = t & 15, ty = t >> 4, warp = t >> 5;
     const int gx0 = 2 + 2 * lx, gy0 = 2 + ty;
@@ -391,12 +390,10 @@ __global__ void __launch_bounds__(PNT, 1) k_fused_pair(const __grid_constant__ S
     const u32 bar = smem_addr(&s_bar);
     u32 parity = 0;                  // phase parity of the next copy to wait for
     u32 issued = 0;                  // copies issued (thread 0)
+    bool expired = false;            // this thread's wait expired: no further waits or copies
 
     if (warp == 0) tm_alloc(&s_tmem, P_TMEM_COLS);
-    if (t == 0) {
-        mbar_init(bar);
-        s_fail = 0;
-    }
+    if (t == 0) mbar_init(bar);
     tm_fence_before();
     __syncthreads();
     tm_fence_after();
@@ -409,7 +406,7 @@ __global__ void __launch_bounds__(PNT, 1) k_fused_pair(const __grid_constant__ S
         s_item[0] = first;
         if (first < A.total_items) {
             const ItemPos P0 = item_pos<PTY>(A, first);
-            if (A.inst[P0.k].tma && !(A.flags & kStepDropCopies)) {
+            if (A.inst[P0.k].tma) {
                 issue_plane<T, PTY>(A, P0, P0.z0 - 2, stage_addr, bar);
                 ++issued;
             }
@@ -496,7 +493,7 @@ __global__ void __launch_bounds__(PNT, 1) k_fused_pair(const __grid_constant__ S
                     m_store2(I, m, h_idx, L.r3[2], ring2(p), L.cf[2]);
                 }
                 if (tma) {
-                    if (!s_fail && !mbar_wait(bar, parity)) s_fail = 1;
+                    if (!expired && !mbar_wait(bar, parity)) expired = true;
                     parity ^= 1u;
                 }
                 {
@@ -513,17 +510,16 @@ __global__ void __launch_bounds__(PNT, 1) k_fused_pair(const __grid_constant__ S
             if (t == 0) {
                 if (p == z0 - 2) s_item[slot ^ 1] = next_t0;
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                if (s_fail || (A.flags & kStepDropCopies)) {
-                } else if (p < z1 + 1) {
+                if (p < z1 + 1) {
                     if (tma) {
-                        issue_plane<T, PTY>(A, P, p + 1, stage_addr, bar);
-                        ++issued;
+                        issue_plane<T, PTY>(A, P, p + 1, stage_addr, bar, expired ? 0u : 1u);
+                        issued += expired ? 0u : 1u;
                     }
                 } else if (next_t0 < A.total_items) {
                     const ItemPos Pn = item_pos<PTY>(A, next_t0);
                     if (A.inst[Pn.k].tma) {
-                        issue_plane<T, PTY>(A, Pn, Pn.z0 - 2, stage_addr, bar);
-                        ++issued;
+                        issue_plane<T, PTY>(A, Pn, Pn.z0 - 2, stage_addr, bar, expired ? 0u : 1u);
+                        issued += expired ? 0u : 1u;
                     }
                 }
             }
@@ -599,12 +595,14 @@ __global__ void __launch_bounds__(PNT, 1) k_fused_pair(const __grid_constant__ S
     }
 
     if (t == 0 && A.total_items > (int)gridDim.x) release_work_counters(A.work);
-    if (s_fail && t == 0) {
-        // the copy whose wait expired may still be in flight: wait for its
-        // phase once more, bounded, before the shared memory is released
-        if (issued > 0) mbar_wait(bar, (issued - 1u) & 1u);
+    if (expired) {
+        // thread 0: the copy whose wait expired may still be in flight: wait
+        // for its phase once more, bounded, before the shared memory is
+        // released
+        if (t == 0 && issued > 0) mbar_wait(bar, (issued - 1u) & 1u);
         atomicOr(A.status, kFlagTimeout);
     }
+    tm_wait_st();   // no TMEM store may be pending when the columns are freed
     tm_fence_before();
     __syncthreads();
     tm_fence_after();

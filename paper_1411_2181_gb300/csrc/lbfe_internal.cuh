@@ -134,9 +134,6 @@ __device__ __forceinline__ float peterlin(float L2, float cxx, float cyy, float 
 constexpr unsigned kFlagDiverged = 1u;
 constexpr unsigned kFlagTimeout = 2u;    // a bounded device-side wait expired (launch status only)
 
-// Step-kernel flags (StepArgs::flags)
-constexpr unsigned kStepDropCopies = 1u;   // test hook: issue no TMA copy, so that the waits expire
-
 // Launchers (lbfe_fused.cu, lbfe_fields.cu, lbfe_obs.cu).
 struct LaunchCtx {
     const InstDev *inst_dev;         // device copy of the descriptors
@@ -149,7 +146,6 @@ struct LaunchCtx {
     const int *item_off_host;        // host copy of item_off
     int total_items, fused_grid, tile_y;
     int step_kernel;                 // lbfe_step_kernel
-    unsigned step_flags = 0;         // StepArgs::flags (test hooks)
     int fused_slots;                 // resident blocks of the fused kernel on the GPU
     const struct PopMaps *maps_host; // per instance: TMA maps of the step kernel (may be null)
     const struct StepMaps *maps_dev; // device copies, [instance][parity]
@@ -169,7 +165,9 @@ struct PopMaps {
     StepMaps m[2];
     int ok;
 };
-cudaError_t fused_pop_maps(const InstDev &I, int precision, int tile_y, PopMaps *m);
+// short_box (test hook): population boxes one row short of what the step
+// kernel expects, so that its waits for them expire
+cudaError_t fused_pop_maps(const InstDev &I, int precision, int tile_y, bool short_box, PopMaps *m);
 cudaError_t launch_fused(const LaunchCtx &c, int cur);
 // Kernel launches of one time step of n instances.
 int fused_launches(int n);

@@ -92,7 +92,6 @@ static_assert(sizeof(StepInst) <= 144, "compact launch descriptor");
 // (the results of an instance are bitwise the same alone or in a batch).
 struct StepArgs {
     int n, total_items;
-    unsigned flags;                // kStep* bits
     unsigned *status;              // status word of the launch
     unsigned *work;                // [0] work-item counter, [1] finished blocks; zero between launches
     int item_off[kStepMaxInst + 1];  // first work item of each instance
@@ -184,6 +183,31 @@ __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
+}
+// Predicated forms (go = 0: nothing is issued), so that the issuing code
+// takes the same path whether or not a copy goes out.
+__device__ __forceinline__ void mbar_expect_p(u32 bar, u32 bytes, u32 go) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t"
+        "@p mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n\t}" ::"r"(bar),
+        "r"(bytes), "r"(go)
+        : "memory");
+}
+__device__ __forceinline__ void tma_box3_p(const CUtensorMap *map, u32 dst, u32 bar, int x, int y, int z, u32 go) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %6, 0;\n\t"
+        "@p cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];\n\t}" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(bar), "r"(go)
+        : "memory");
+}
+__device__ __forceinline__ void tma_box4_p(const CUtensorMap *map, u32 dst, u32 bar, int x, int y, int z, u32 go) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %7, 0;\n\t"
+        "@p cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];\n\t}" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(0), "r"(bar), "r"(go)
+        : "memory");
 }
 // Wait for the completion of phase `parity`; false once the limit expired.
 __device__ __forceinline__ bool mbar_wait(u32 bar, u32 parity) {
@@ -755,19 +779,20 @@ __device__ __forceinline__ ItemPos item_pos(const StepArgs &A, int item) {
 }
 
 template <typename T, int TY>
-__device__ __forceinline__ void issue_plane(const StepArgs &A, const ItemPos &P, int plane, u32 dst, u32 bar) {
+__device__ __forceinline__ void issue_plane(const StepArgs &A, const ItemPos &P, int plane, u32 dst, u32 bar,
+                                            u32 go = 1u) {
     using St = Stage<T, TY>;
     const StepInst &I = A.inst[P.k];
     const int z = min(max(plane, 0), I.Lz - 1);
     if (St::REGION) {
         const bool dcopy = St::DENS && I.dens_in != nullptr;   // offset densities tracked per cell
-        mbar_expect(bar, St::POP_BYTES + St::C_BYTES + (dcopy ? St::D_BYTES : 0u));
-        tma_box4(&I.maps->pop, dst, bar, P.bx * 32 - St::XPAD, P.by * TY - 2, z);
-        tma_box4(&I.maps->c, dst + St::C_OFF, bar, P.bx * 32 - 4, P.by * TY - 2, z);
-        if (dcopy) tma_box3(&I.maps->dens, dst + St::D_OFF, bar, P.bx * 32 - 2, P.by * TY - 2, z);
+        mbar_expect_p(bar, St::POP_BYTES + St::C_BYTES + (dcopy ? St::D_BYTES : 0u), go);
+        tma_box4_p(&I.maps->pop, dst, bar, P.bx * 32 - St::XPAD, P.by * TY - 2, z, go);
+        tma_box4_p(&I.maps->c, dst + St::C_OFF, bar, P.bx * 32 - 4, P.by * TY - 2, z, go);
+        if (dcopy) tma_box3_p(&I.maps->dens, dst + St::D_OFF, bar, P.bx * 32 - 2, P.by * TY - 2, z, go);
     } else {
-        mbar_expect(bar, St::POP_BYTES);
-        tma_box4(&I.maps->pop, dst, bar, P.bx * 32, P.by * TY, z);
+        mbar_expect_p(bar, St::POP_BYTES, go);
+        tma_box4_p(&I.maps->pop, dst, bar, P.bx * 32, P.by * TY, z, go);
     }
 }
 

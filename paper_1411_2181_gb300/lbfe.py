@@ -25,7 +25,7 @@ _lib = ct.CDLL(LIB_PATH)
 
 FIELD_F, FIELD_C, FIELD_RHO, FIELD_U = 0, 1, 2, 3
 STEP_CELL, STEP_PAIR = 0, 1   # lbfe_step_kernel
-INJECT_DROP_COPIES = 1        # lbfe_test_inject
+INJECT_SHORT_COPIES = 1       # lbfe_test_inject
 
 OK, ERR_BAD_PARAM, ERR_NO_MEMORY, ERR_CUDA, ERR_DIVERGED, ERR_TIMEOUT, ERR_STATE = range(7)
 

@@ -82,4 +82,4 @@ def test_create_rejects_small_or_misaligned_block(lbfe):
 
 
 def test_test_inject_rejects_null_handle(lbfe):
-    assert lbfe._lib.lbfe_test_inject(None, lbfe.INJECT_DROP_COPIES) == lbfe.ERR_BAD_PARAM
+    assert lbfe._lib.lbfe_test_inject(None, lbfe.INJECT_SHORT_COPIES) == lbfe.ERR_BAD_PARAM

@@ -1,8 +1,9 @@
-"""Failure path of the step kernel: a TMA copy that never arrives.  The test
-hook makes the kernel issue no copies; every block's bounded wait for its
-first copy expires (after about a second of GPU time), the block finishes
-its work items without waiting again, and the host reads LBFE_ERR_TIMEOUT.
-The context stays usable: a new solver steps and matches the oracle."""
+"""Failure path of the step kernel: a TMA copy whose completion never comes.
+The test hook rebuilds the population tensor maps one row short of what the
+kernel expects, so that the completion barrier of each block's first copy
+stays pending; the bounded wait expires (after about a second of GPU time),
+the block stops, and the host reads LBFE_ERR_TIMEOUT.  The context stays
+usable: a new solver on it steps and matches the oracle."""
 import time
 
 import numpy as np
@@ -28,7 +29,7 @@ def test_expired_copy_wait_reports_timeout(L, kernel, ty):
     s = L.Solver(p)
     s.tune(ty, 0, kernel)
     s.init(0, rho)
-    s.test_inject(L.INJECT_DROP_COPIES)
+    s.test_inject(L.INJECT_SHORT_COPIES)
     t0 = time.time()
     s.step(1)
     st = s.check()
