@@ -215,12 +215,7 @@ __device__ __forceinline__ void m_load2_staged(const StepInst &I, const T *stage
 // Moments, stress scalars and conformation of the pair at ring index idx
 // (even) into the ring slots of its plane.
 __device__ __forceinline__ void m_store2(const StepInst &I, const MPair &m, int idx, int s3, int s2, int s4) {
-    constexpr int R2N = PG::R2N;
     using Rg = Ring<PTY>;
-    float2 *rho_s = reinterpret_cast<float2 *>(smem() + Rg::RHO) + s3 * R2N;
-    float *pi_s = smem() + Rg::PI + s3 * 2 * R2N;
-    float *j_s = smem() + Rg::J + s2 * 3 * R2N;
-    float *c_s = smem() + Rg::C + s4 * 6 * R2N;
     float2 rA = make_float2(0.f, 0.f), rB = make_float2(0.f, 0.f);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -236,12 +231,14 @@ __device__ __forceinline__ void m_store2(const StepInst &I, const MPair &m, int 
         if (cy(i)) jy = cy(i) > 0 ? add2(jy, d) : sub2(jy, d);
         if (cz(i)) jz = cz(i) > 0 ? add2(jz, d) : sub2(jz, d);
     }
-    *reinterpret_cast<float4 *>(rho_s + idx) = make_float4(rA.x, rB.x, rA.y, rB.y);
-    *reinterpret_cast<float2 *>(j_s + idx) = jx;
-    *reinterpret_cast<float2 *>(j_s + R2N + idx) = jy;
-    *reinterpret_cast<float2 *>(j_s + 2 * R2N + idx) = jz;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) *reinterpret_cast<float2 *>(c_s + k * R2N + idx) = m.c[k];
+    // both cells (idx even) in one 16-byte store per ring array
+    *reinterpret_cast<float4 *>(Rg::rho(s3) + idx) = make_float4(rA.x, rB.x, rA.y, rB.y);
+    *reinterpret_cast<float4 *>(Rg::jxy(s2) + idx) = make_float4(jx.x, jy.x, jx.y, jy.y);
+    *reinterpret_cast<float2 *>(Rg::jz(s2) + idx) = jz;
+    // C components xx, yy, zz, xy, xz, yz = m.c[0..5]; pairs (xx, xy), (yy, yz), (xz, zz)
+    *reinterpret_cast<float4 *>(Rg::c(s4, 0) + idx) = make_float4(m.c[0].x, m.c[3].x, m.c[0].y, m.c[3].y);
+    *reinterpret_cast<float4 *>(Rg::c(s4, 1) + idx) = make_float4(m.c[1].x, m.c[5].x, m.c[1].y, m.c[5].y);
+    *reinterpret_cast<float4 *>(Rg::c(s4, 2) + idx) = make_float4(m.c[4].x, m.c[2].x, m.c[4].y, m.c[2].y);
     float2 af = make_float2(0.f, 0.f), a = af;
     if (I.visc_comp >= 0) {
         const float2 rv = I.visc_comp == 0 ? rA : rB;
@@ -250,8 +247,7 @@ __device__ __forceinline__ void m_store2(const StepInst &I, const MPair &m, int 
         af.x = a.x * peterlin(I.L2, m.c[0].x, m.c[1].x, m.c[2].x);
         af.y = a.y * peterlin(I.L2, m.c[0].y, m.c[1].y, m.c[2].y);
     }
-    *reinterpret_cast<float2 *>(pi_s + idx) = af;
-    *reinterpret_cast<float2 *>(pi_s + R2N + idx) = a;
+    *reinterpret_cast<float4 *>(Rg::pi(s3) + idx) = make_float4(af.x, a.x, af.y, a.y);
 }
 
 // Pair (gx, gy) of the radius-2 region outside the tile, h < NPAIR_HALO:

@@ -352,16 +352,32 @@ __device__ __forceinline__ void ring2_coord(int h, int &gx, int &gy) {
     }
 }
 
-// Shared-memory rings (offsets in floats from the dynamic shared base):
-//   rho  float2 [3][R2N]          densities rho_A, rho_B
-//   pi   float  [3][2][R2N]       a f and a of Pi = a (f C) - a I, a = (eta_P/tau_P) chi
-//   j    float  [2][3][R2N]       momentum
-//   c    float  [4][6][R2N]       conformation
-//   u    float  [3][3][R2N]       velocity
+extern __shared__ float4 lbfe_smem4[];
+__device__ __forceinline__ float *smem() { return reinterpret_cast<float *>(lbfe_smem4); }
+
+// Shared-memory rings (offsets in floats from the dynamic shared base).
+// Values read together sit in pairs, so that one 8-byte access serves two:
+//   rho  float2 [3][R2N]          (rho_A, rho_B)
+//   pi   float2 [3][R2N]          (a f, a) of Pi = a (f C) - a I, a = (eta_P/tau_P) chi
+//   j    [2] x (float2 [R2N] (j_x, j_y), float [R2N] j_z)          momentum
+//   c    [4] x float2 [3][R2N]: (xx, xy), (yy, yz), (xz, zz)       conformation
+//   u    [3] x (float2 [R2N] (u_x, u_y), float [R2N] u_z)          velocity
+// (the pairs of C give each axis of the divergence and of the upwind
+// stencil its three components in two 8-byte reads).  R2N is a multiple of
+// 4, so every array starts on a 16-byte boundary.
 template <int TY>
 struct Ring {
     static constexpr int R2N = Geom<TY>::R2N;
+    static_assert(R2N % 4 == 0, "ring alignment");
     static constexpr int RHO = 0, PI = 6 * R2N, J = PI + 6 * R2N, C = J + 6 * R2N, U = C + 24 * R2N;
+    __device__ static float2 *rho(int s) { return reinterpret_cast<float2 *>(smem() + RHO) + s * R2N; }
+    __device__ static float2 *pi(int s) { return reinterpret_cast<float2 *>(smem() + PI) + s * R2N; }
+    __device__ static float2 *jxy(int s) { return reinterpret_cast<float2 *>(smem() + J + s * 3 * R2N); }
+    __device__ static float *jz(int s) { return smem() + J + s * 3 * R2N + 2 * R2N; }
+    // pair k (0: (xx, xy), 1: (yy, yz), 2: (xz, zz)) of C slot s
+    __device__ static float2 *c(int s, int k) { return reinterpret_cast<float2 *>(smem() + C + (s * 3 + k) * 2 * R2N); }
+    __device__ static float2 *uxy(int s) { return reinterpret_cast<float2 *>(smem() + U + s * 3 * R2N); }
+    __device__ static float *uz(int s) { return smem() + U + s * 3 * R2N + 2 * R2N; }
 };
 
 // TMA staging of one plane.  TY = 16: the tile's own populations (box
@@ -391,8 +407,6 @@ struct Stage {
     static constexpr u32 BYTES = (D_OFF + D_BYTES + 127u) & ~127u;
 };
 
-extern __shared__ float4 lbfe_smem4[];
-__device__ __forceinline__ float *smem() { return reinterpret_cast<float *>(lbfe_smem4); }
 
 // Packed FP32 (two lanes per instruction).
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -481,12 +495,7 @@ __device__ __forceinline__ void m_load_region(const StepInst &I, const T *sp, co
 template <int TY>
 __device__ __forceinline__ void m_store(const StepInst &I, const MCell &m, int idx, int s3, int s2, int s4) {
     // s3: rho / stress slot, s2: j slot, s4: C slot of the plane
-    constexpr int R2N = Geom<TY>::R2N;
     using Rg = Ring<TY>;
-    float2 *rho_s = reinterpret_cast<float2 *>(smem() + Rg::RHO) + s3 * R2N;
-    float *pi_s = smem() + Rg::PI + s3 * 2 * R2N;
-    float *j_s = smem() + Rg::J + s2 * 3 * R2N;
-    float *c_s = smem() + Rg::C + s4 * 6 * R2N;
     float2 r = m.ab[0];
 #pragma unroll
     for (int i = 1; i < Q; ++i) r = add2(r, m.ab[i]);
@@ -498,19 +507,19 @@ __device__ __forceinline__ void m_store(const StepInst &I, const MCell &m, int i
         if (cy(i)) jy = cy(i) > 0 ? add2(jy, d) : sub2(jy, d);
         if (cz(i)) jz = cz(i) > 0 ? add2(jz, d) : sub2(jz, d);
     }
-    rho_s[idx] = r;
-    j_s[idx] = jx.x + jx.y;
-    j_s[R2N + idx] = jy.x + jy.y;
-    j_s[2 * R2N + idx] = jz.x + jz.y;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) c_s[k * R2N + idx] = m.c[k];
+    Rg::rho(s3)[idx] = r;
+    Rg::jxy(s2)[idx] = make_float2(jx.x + jx.y, jy.x + jy.y);
+    Rg::jz(s2)[idx] = jz.x + jz.y;
+    // C components xx, yy, zz, xy, xz, yz = m.c[0..5]
+    Rg::c(s4, 0)[idx] = make_float2(m.c[0], m.c[3]);
+    Rg::c(s4, 1)[idx] = make_float2(m.c[1], m.c[5]);
+    Rg::c(s4, 2)[idx] = make_float2(m.c[4], m.c[2]);
     float a = 0.f, fp = 1.f;
     if (I.visc_comp >= 0) {
         a = I.pi_coef * (I.visc_comp == 0 ? r.x : r.y) / (r.x + r.y);
         fp = peterlin(I.L2, m.c[0], m.c[1], m.c[2]);
     }
-    pi_s[idx] = a * fp;
-    pi_s[R2N + idx] = a;
+    Rg::pi(s3)[idx] = make_float2(a * fp, a);
 }
 
 // Ring slots of the planes one iteration touches (q = p - 1, r = p - 2).
@@ -551,34 +560,50 @@ __device__ __forceinline__ void stage_f_cell(const StepInst &I, int idx, const S
     // Pi_ba = (a f) C_ba - a delta_ba
     float FP[3] = {0.f, 0.f, 0.f};
     if (I.visc_comp >= 0) {
-        const float *sm_ = smem() + Rg::PI + L.r3[0] * 2 * R2N;
-        const float *sc_ = smem() + Rg::PI + L.r3[1] * 2 * R2N;
-        const float *sp_ = smem() + Rg::PI + L.r3[2] * 2 * R2N;
-        const float *cm = smem() + Rg::C + L.cf[0] * 6 * R2N;
-        const float *cc = smem() + Rg::C + L.cf[1] * 6 * R2N;
-        const float *cp = smem() + Rg::C + L.cf[2] * 6 * R2N;
-        const float afxp = sc_[idx + 1], afxm = sc_[idx - 1], afyp = sc_[idx + RX], afym = sc_[idx - RX];
-        const float afzp = sp_[idx], afzm = sm_[idx];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            float gxd = afxp * cc[symk(0, a) * R2N + idx + 1] - afxm * cc[symk(0, a) * R2N + idx - 1];
-            float gyd = afyp * cc[symk(1, a) * R2N + idx + RX] - afym * cc[symk(1, a) * R2N + idx - RX];
-            float gzd = afzp * cp[symk(2, a) * R2N + idx] - afzm * cm[symk(2, a) * R2N + idx];
-            if (a == 0) gxd -= sc_[R2N + idx + 1] - sc_[R2N + idx - 1];
-            if (a == 1) gyd -= sc_[R2N + idx + RX] - sc_[R2N + idx - RX];
-            if (a == 2) gzd -= sp_[R2N + idx] - sm_[R2N + idx];
-            FP[a] = 0.5f * (gxd + gyd + gzd);
-        }
+        const float2 *pc = Rg::pi(L.r3[1]);
+        const float2 Ax = pc[idx + 1], Bx = pc[idx - 1], Ay = pc[idx + RX], By = pc[idx - RX];
+        const float2 Az = Rg::pi(L.r3[2])[idx], Bz = Rg::pi(L.r3[0])[idx];
+        // x-neighbours: C_xx, C_xy (pair 0), C_xz (pair 2)
+        const float2 *c0 = Rg::c(L.cf[1], 0), *c1 = Rg::c(L.cf[1], 1), *c2 = Rg::c(L.cf[1], 2);
+        const float2 xp0 = c0[idx + 1], xm0 = c0[idx - 1];
+        const float xp2 = c2[idx + 1].x, xm2 = c2[idx - 1].x;
+        // y-neighbours: C_xy (pair 0), C_yy, C_yz (pair 1)
+        const float yp0 = c0[idx + RX].y, ym0 = c0[idx - RX].y;
+        const float2 yp1 = c1[idx + RX], ym1 = c1[idx - RX];
+        // z-neighbours (planes q + 1, q - 1): C_xz, C_zz (pair 2), C_yz (pair 1)
+        const float2 zp2 = Rg::c(L.cf[2], 2)[idx], zm2 = Rg::c(L.cf[0], 2)[idx];
+        const float zp1 = Rg::c(L.cf[2], 1)[idx].y, zm1 = Rg::c(L.cf[0], 1)[idx].y;
+        // a = x
+        float gxd = Ax.x * xp0.x - Bx.x * xm0.x;
+        float gyd = Ay.x * yp0 - By.x * ym0;
+        float gzd = Az.x * zp2.x - Bz.x * zm2.x;
+        gxd -= Ax.y - Bx.y;
+        FP[0] = 0.5f * (gxd + gyd + gzd);
+        // a = y
+        gxd = Ax.x * xp0.y - Bx.x * xm0.y;
+        gyd = Ay.x * yp1.x - By.x * ym1.x;
+        gzd = Az.x * zp1 - Bz.x * zm1;
+        gyd -= Ay.y - By.y;
+        FP[1] = 0.5f * (gxd + gyd + gzd);
+        // a = z
+        gxd = Ax.x * xp2 - Bx.x * xm2;
+        gyd = Ay.x * yp1.y - By.x * ym1.y;
+        gzd = Az.x * zp2.y - Bz.x * zm2.y;
+        gzd -= Az.y - Bz.y;
+        FP[2] = 0.5f * (gxd + gyd + gzd);
     }
     const float g[3] = {I.gx, I.gy, I.gz};
     const float inv = 1.0f / (rA + rB);
+    const float2 jxy = Rg::jxy(L.j3)[idx];
+    const float j[3] = {jxy.x, jxy.y, Rg::jz(L.j3)[idx]};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         FA[a] = -I.G * rA * sA[a] + (rA * inv) * FP[a] + rA * g[a];
         FB[a] = -I.G * rB * sB[a] + (rB * inv) * FP[a] + rB * g[a];
-        u[a] = (smem()[Rg::J + L.j3 * 3 * R2N + a * R2N + idx] + 0.5f * (FA[a] + FB[a])) * inv;
-        smem()[Rg::U + L.r3[1] * 3 * R2N + a * R2N + idx] = u[a];
+        u[a] = (j[a] + 0.5f * (FA[a] + FB[a])) * inv;
     }
+    Rg::uxy(L.r3[1])[idx] = make_float2(u[0], u[1]);
+    Rg::uz(L.r3[1])[idx] = u[2];
 }
 
 // Stage U for one cell (ring index idx) of plane r: the FENE-P update of
@@ -587,42 +612,51 @@ __device__ __forceinline__ void stage_f_cell(const StepInst &I, int idx, const S
 // new conformation to cn; returns false when tr C reached L^2.
 template <int TY>
 __device__ __forceinline__ bool stage_u_cell(const StepInst &I, int idx, const Slots &L, int r, float cn[6]) {
-    constexpr int R2N = Geom<TY>::R2N, RX = Geom<TY>::RX;
+    constexpr int RX = Geom<TY>::RX;
     using Rg = Ring<TY>;
     const float Uw = I.Uw;
     const int Lz = I.Lz;
-    const float *um = smem() + Rg::U + L.ur[0] * 3 * R2N;
-    const float *uc = smem() + Rg::U + L.ur[1] * 3 * R2N;
-    const float *up = smem() + Rg::U + L.ur[2] * 3 * R2N;
-    const float *cm = smem() + Rg::C + L.cu[0] * 6 * R2N;
-    const float *cc = smem() + Rg::C + L.cu[1] * 6 * R2N;
-    const float *cp = smem() + Rg::C + L.cu[2] * 6 * R2N;
-    float u0[3], Gr[3][3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) u0[j] = uc[j * R2N + idx];
+    const float2 *uxc = Rg::uxy(L.ur[1]);
+    const float *uzc = Rg::uz(L.ur[1]);
+    const float2 u01 = uxc[idx];
+    const float u0[3] = {u01.x, u01.y, uzc[idx]};
+    // neighbours of plane r along x and y, and of the own column in z
+    const float2 axp = uxc[idx + 1], axm = uxc[idx - 1], ayp = uxc[idx + RX], aym = uxc[idx - RX];
+    const float zxp = uzc[idx + 1], zxm = uzc[idx - 1], zyp = uzc[idx + RX], zym = uzc[idx - RX];
+    const float2 up01 = Rg::uxy(L.ur[2])[idx], um01 = Rg::uxy(L.ur[0])[idx];
+    const float upn[3] = {up01.x, up01.y, Rg::uz(L.ur[2])[idx]};
+    const float umn[3] = {um01.x, um01.y, Rg::uz(L.ur[0])[idx]};
+    const float uxp[3] = {axp.x, axp.y, zxp}, uxm[3] = {axm.x, axm.y, zxm};
+    const float uyp[3] = {ayp.x, ayp.y, zyp}, uym[3] = {aym.x, aym.y, zym};
+    float Gr[3][3];
     // grad u by central differences, u_ghost = 2 U_wall - u at the walls
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         const float uwb = j == 0 ? -Uw : 0.f, uwt = j == 0 ? Uw : 0.f;
-        const float uzp = (r == Lz - 1) ? 2.f * uwt - u0[j] : up[j * R2N + idx];
-        const float uzm = (r == 0) ? 2.f * uwb - u0[j] : um[j * R2N + idx];
-        Gr[0][j] = 0.5f * (uc[j * R2N + idx + 1] - uc[j * R2N + idx - 1]);
-        Gr[1][j] = 0.5f * (uc[j * R2N + idx + RX] - uc[j * R2N + idx - RX]);
+        const float uzp = (r == Lz - 1) ? 2.f * uwt - u0[j] : upn[j];
+        const float uzm = (r == 0) ? 2.f * uwb - u0[j] : umn[j];
+        Gr[0][j] = 0.5f * (uxp[j] - uxm[j]);
+        Gr[1][j] = 0.5f * (uyp[j] - uym[j]);
         Gr[2][j] = 0.5f * (uzp - uzm);
     }
-    float c[6];
-#pragma unroll
-    for (int q6 = 0; q6 < 6; ++q6) c[q6] = cc[q6 * R2N + idx];
+    // C components xx, yy, zz, xy, xz, yz from the pairs (xx, xy), (yy, yz), (xz, zz)
+    auto c_at = [&](int s, int n, float out[6]) {
+        const float2 p0 = Rg::c(s, 0)[n], p1 = Rg::c(s, 1)[n], p2 = Rg::c(s, 2)[n];
+        out[0] = p0.x; out[1] = p1.x; out[2] = p2.y; out[3] = p0.y; out[4] = p2.x; out[5] = p1.y;
+    };
+    float c[6], cx_[6], cy_[6], cz6[6];
+    c_at(L.cu[1], idx, c);
     // first-order upwind u . grad C (C mirrored at the walls)
     const int ox = u0[0] > 0.f ? -1 : 1, oy = u0[1] > 0.f ? -RX : RX;
     const float sx = u0[0] > 0.f ? u0[0] : -u0[0], sy = u0[1] > 0.f ? u0[1] : -u0[1];
     const float sz = u0[2] > 0.f ? u0[2] : -u0[2];
-    const float *cz_ = u0[2] > 0.f ? cm : cp;
+    c_at(L.cu[1], idx + ox, cx_);
+    c_at(L.cu[1], idx + oy, cy_);
+    c_at(u0[2] > 0.f ? L.cu[0] : L.cu[2], idx, cz6);
     float adv[6];
 #pragma unroll
     for (int q6 = 0; q6 < 6; ++q6)
-        adv[q6] = sx * (c[q6] - cc[q6 * R2N + idx + ox]) + sy * (c[q6] - cc[q6 * R2N + idx + oy]) +
-                  sz * (c[q6] - cz_[q6 * R2N + idx]);
+        adv[q6] = sx * (c[q6] - cx_[q6]) + sy * (c[q6] - cy_[q6]) + sz * (c[q6] - cz6[q6]);
     const float Cm[3][3] = {{c[0], c[3], c[4]}, {c[3], c[1], c[5]}, {c[4], c[5], c[2]}};
     const float fp = peterlin(I.L2, c[0], c[1], c[2]);
 #pragma unroll
