@@ -333,11 +333,24 @@ def run_ours(a):
                "dtype": DTYPE[prec], "data": "synthetic (seeded droplet, NumPy PCG64)",
                "config": dict(config_dict(a.workload, ps), launch=launch), "roofline": roof, "cpu_baseline": cpu,
                "e2e": e2e, "clocks": clk.summary(), "gpu_launches": s.launches_per_step() * a.steps,
+               "autotune": autotune_summary(shape),
                "status": lbfe._lib.lbfe_status_str(st).decode(),
                "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
         print(json.dumps(out))
     if dist:
         tdist.destroy_process_group()
+
+
+def autotune_summary(shape):
+    """Fastest measured step time (ms) of each kernel variant and tile height
+    over the z-chunks the autotuner tried on this GPU."""
+    if not shape:
+        return None
+    best = {}
+    for kern, ty, _zc, ms in shape.get("trials", []):
+        key = f"{'pair' if kern else 'cell'}_32x{ty}"
+        best[key] = round(min(ms, best.get(key, ms)), 5)
+    return {"best_ms_per_step": best}
 
 
 # ---------------------------------------------------------------- reference arm
