@@ -41,7 +41,8 @@ k_fused(const __grid_constant__ StepArgs A) {
     // its cells from the staging buffer, issued by lane 0 of the last warp
     // (which has no halo cells in stage M), instead of by thread 0 after
     // the stage-M barrier.  Measured on 192 x 96 x 80: 158 -> 148 us per
-    // step at 32 x 8; slower for the other shapes (140 -> 160 us at 32 x 12).
+    // step at 32 x 8 (142 us with the staged halo cell read before the own
+    // cell); slower for the other shapes (140 -> 160 us at 32 x 12).
     constexpr bool kEarlyIssue = TY == 8 && sizeof(T) == 4;
     constexpr int kIssuer = kEarlyIssue ? NT - 32 : 0;
     static_assert(!St::REGION || MH == 1, "one stage-M halo cell per thread");
@@ -134,8 +135,8 @@ k_fused(const __grid_constant__ StepArgs A) {
             h_dom[r] = xg >= 0 && xg < Lx && yg >= 0 && yg < Ly;
         }
 
-        // this thread's last read of the staging buffer is its halo cell
-        const bool late = St::REGION && tma && h_on[0] && h_dom[0];
+        // this thread has a halo cell staged in the region copy
+        const bool staged_halo = St::REGION && tma && h_on[0] && h_dom[0];
         float FA[3], FB[3], uo[3], rAo = 1.f, rBo = 0.f;
 
         for (int p = z0 - 2; p <= z1 + 1; ++p) {
@@ -180,6 +181,10 @@ k_fused(const __grid_constant__ StepArgs A) {
                     if (!expired && !mbar_wait(bar, parity)) expired = true;
                     parity ^= 1u;
                 }
+                // early issue: the staged halo cell is read first, so that every
+                // thread is done with the staging buffer after its own cell
+                if (kEarlyIssue && St::REGION && staged_halo)
+                    m_load_region<T, TY>(I, stage, stage_c, h_gx[0], h_gy[0], pl + h_ofs[0], mh[0]);
                 {
                     // own cell; its populations wait in TMEM for stage X(p)
                     MCell m;
@@ -191,8 +196,9 @@ k_fused(const __grid_constant__ StepArgs A) {
                     } else {
                         m_load<T>(I, fin, Cin, S, pl + ofs_in, m);
                     }
-                    // done with the staging buffer (unless a staged halo cell follows)
-                    if (kEarlyIssue && !late) mbar_arrive(ebar);
+                    // done with the staging buffer (early issue reads the staged
+                    // halo cell before the own cell)
+                    if (kEarlyIssue) mbar_arrive(ebar);
                     m_store<TY>(I, m, idx_in, L.r3[2], ring2(p), L.cf[2]);
                     tm_store38(tm_warp + (u32)((p & 1) * 64), reinterpret_cast<const float *>(m.ab));
                 }
@@ -200,9 +206,8 @@ k_fused(const __grid_constant__ StepArgs A) {
 #pragma unroll
                     for (int rr = 0; rr < MH; ++rr)
                         if (h_on[rr]) {
-                            if (tma && h_dom[rr])
+                            if (!kEarlyIssue && tma && h_dom[rr])
                                 m_load_region<T, TY>(I, stage, stage_c, h_gx[rr], h_gy[rr], pl + h_ofs[rr], mh[rr]);
-                            if (kEarlyIssue && late) mbar_arrive(ebar);
                             m_store<TY>(I, mh[rr], h_idx[rr], L.r3[2], ring2(p), L.cf[2]);
                         }
                 }

@@ -44,7 +44,9 @@
 //    storage forms, the offset densities: one box each); tiles
 //    of 16 rows copy their own cells and read the halo with ordinary loads.
 //    Cells across a periodic seam and ragged-tile cells use ordinary loads
-//    (through L2 only: the large shared carve-out leaves little L1).
+//    (through L2 only: the large shared carve-out leaves little L1).  For
+//    FP32 8-row tiles the next copy starts once every thread has read the
+//    staging buffer (a second mbarrier), before the stage-M barrier.
 //  * TMEM handoff: each thread's own-cell populations, decoded to FP32 in
 //    stage M(p), wait in tensor memory for the collision X(p) one plane
 //    later (two plane buffers of 38 columns per warp in its 32-lane quarter,
