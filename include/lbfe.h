@@ -193,6 +193,8 @@ typedef enum {
 /* Launch shape of the step kernel: variant (lbfe_step_kernel), column-tile
  * height tile_y (tile width 32; 16 for LBFE_STEP_PAIR) and z-chunk depth in
  * planes (0 = automatic: fill the resident blocks of the GPU about once).
+ * A new handle starts with LBFE_STEP_CELL, tile_y 8 (FP32) or 12 (FP16 /
+ * BF16 storage) and the automatic z-chunk.
  * LBFE_ERR_BAD_PARAM for an unsupported combination.  Synchronises the
  * stream. */
 lbfe_status lbfe_tune(lbfe_handle *h, int step_kernel, int tile_y, int z_chunk);

@@ -267,3 +267,14 @@ def test_graph_replay_equals_single_steps(L):
     fa, Ca = run(True)
     fb, Cb = run(False)
     assert np.array_equal(fa, fb) and np.array_equal(Ca, Cb)
+
+
+@pytest.mark.parametrize("prec,tile_y", [(0, 8), (1, 12), (2, 12)])
+def test_default_launch_shape(L, prec, tile_y):
+    """A new handle starts with one cell per thread, 8-row tiles in FP32 and
+    12-row tiles with 2-byte storage, z-chunk chosen automatically."""
+    p, _, _ = configs.config1()
+    s = L.Solver(replace(p, precision=prec))
+    cfg = s.launch_config()
+    s.close()
+    assert cfg["kernel"] == L.STEP_CELL and cfg["tile_y"] == tile_y and cfg["z_chunk"] >= 8
