@@ -17,8 +17,8 @@ k_fused(const __grid_constant__ StepArgs A) {
     using St = Stage<T, TY>;
     using Rg = Ring<TY>;
     // interior planes take a push without the bounce-back selection where
-    // registers allow the second copy of the collision
-    constexpr bool kSplitWalls = TY <= 8;
+    // registers allow the second copy of the collision (not at 16 rows)
+    constexpr bool kSplitWalls = TY <= 12;
     // the collision's TMEM loads are issued before stage F where registers
     // allow holding them through it
     constexpr bool kEarlyTmem = TY <= 8;
