@@ -52,7 +52,8 @@ typedef enum {
     LBFE_ERR_CUDA = 3,        /* a CUDA runtime call failed (see lbfe_last_cuda_error) */
     LBFE_ERR_DIVERGED = 4,    /* the device flagged a numerical blow-up */
     LBFE_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired */
-    LBFE_ERR_STATE = 6        /* call out of order, e.g. step before init */
+    LBFE_ERR_STATE = 6,       /* call out of order, e.g. step before init */
+    LBFE_ERR_IO = 7           /* checkpoint file unreadable, unwritable, truncated or corrupt */
 } lbfe_status;
 
 typedef enum {
@@ -246,6 +247,27 @@ lbfe_status lbfe_test_inject(lbfe_handle *h, unsigned what);
  * routine. */
 lbfe_status lbfe_observables_noalloc(const lbfe_params *p, const void *f_dev, long long stride, lbfe_obs *out,
                                      void *stream);
+
+/* Checkpoint / resume of instance k (not in the paper: its runs are single
+ * long integrations).  lbfe_save writes the instance's state after its last
+ * step: the parameter set, the step count, the populations (the storage
+ * type, [2][19][N] without the stride padding), C ([6][N] float32) and, in
+ * the reduced forms, the per-cell offset densities ([N] pairs of float32),
+ * into one raw little-endian file at path, behind a header that carries a
+ * CRC-32 of itself and one of the payload (lbfe_crc32).  lbfe_load reads such
+ * a file into instance k of a handle created with the same parameter set
+ * (compared byte for byte: BAD_PARAM otherwise) and makes it ready to step;
+ * resumed runs are bitwise identical to uninterrupted ones at the same
+ * launch shape.  IO for a file that cannot be opened, read or written, is
+ * truncated, or fails a CRC.  Both synchronise the stream; BAD_PARAM for a
+ * null handle or path or k out of range, STATE for lbfe_save before
+ * lbfe_init. */
+lbfe_status lbfe_save(lbfe_handle *h, int k, const char *path);
+lbfe_status lbfe_load(lbfe_handle *h, int k, const char *path);
+
+/* CRC-32 (reflected polynomial 0xEDB88320, the one of zlib and PNG) of n
+ * bytes, continuing from crc (0 to start); host only. */
+unsigned lbfe_crc32(const void *data, size_t n, unsigned crc);
 
 /* Release the handle (the device block stays the caller's). */
 lbfe_status lbfe_destroy(lbfe_handle *h);

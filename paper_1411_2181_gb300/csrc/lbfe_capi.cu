@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -339,6 +340,7 @@ const char *lbfe_status_str(lbfe_status s) {
         case LBFE_ERR_DIVERGED: return "simulation diverged";
         case LBFE_ERR_TIMEOUT: return "device wait timed out";
         case LBFE_ERR_STATE: return "call out of order";
+        case LBFE_ERR_IO: return "checkpoint file unreadable, unwritable or corrupt";
     }
     return "unknown status";
 }
@@ -724,6 +726,125 @@ lbfe_status lbfe_launch_config(const lbfe_handle *h, int *step_kernel, int *tile
     if (z_chunk) *z_chunk = h->inst[0].zc;
     if (grid) *grid = h->fused_grid;
     if (items) *items = h->total_items;
+    return LBFE_OK;
+}
+
+unsigned lbfe_crc32(const void *data, size_t n, unsigned crc) {
+    // table-driven CRC-32, reflected polynomial 0xEDB88320
+    static unsigned table[256];
+    static std::once_flag once;
+    std::call_once(once, [] {
+        for (unsigned i = 0; i < 256; ++i) {
+            unsigned c = i;
+            for (int b = 0; b < 8; ++b) c = (c & 1u) ? 0xEDB88320u ^ (c >> 1) : c >> 1;
+            table[i] = c;
+        }
+    });
+    const unsigned char *p = static_cast<const unsigned char *>(data);
+    crc = ~crc;
+    for (size_t i = 0; i < n; ++i) crc = table[(crc ^ p[i]) & 0xFFu] ^ (crc >> 8);
+    return ~crc;
+}
+
+namespace {
+
+// Checkpoint file: this header, then populations, C and offset densities.
+struct CkptHeader {
+    char magic[8];                   // "LBFECKPT"
+    unsigned version;                // 1
+    unsigned header_bytes;           // sizeof(CkptHeader)
+    lbfe_params params;
+    long long steps, cells;
+    unsigned precision, elem_bytes;
+    unsigned long long f_bytes, c_bytes, d_bytes;
+    unsigned payload_crc;
+    unsigned header_crc;             // CRC of the header with this field zero
+};
+constexpr char kCkptMagic[8] = {'L', 'B', 'F', 'E', 'C', 'K', 'P', 'T'};
+
+unsigned header_crc(CkptHeader hd) {
+    hd.header_crc = 0;
+    return lbfe_crc32(&hd, sizeof hd, 0);
+}
+
+struct FileCloser {
+    FILE *f;
+    ~FileCloser() {
+        if (f) std::fclose(f);
+    }
+};
+
+}  // namespace
+
+lbfe_status lbfe_save(lbfe_handle *h, int k, const char *path) {
+    if (!h || !path || k < 0 || k >= h->n) return LBFE_ERR_BAD_PARAM;
+    if (!h->ready[k]) return LBFE_ERR_STATE;
+    const InstDev &I = h->inst[k];
+    const size_t N = (size_t)I.N, S = (size_t)I.S, eb = elem_bytes(h->precision);
+    const bool dens = h->precision != LBFE_FP32 && I.dens[0] != nullptr;
+    CkptHeader hd{};
+    std::memcpy(hd.magic, kCkptMagic, 8);
+    hd.version = 1;
+    hd.header_bytes = sizeof hd;
+    hd.params = h->params[k];
+    hd.steps = h->steps[k];
+    hd.cells = I.N;
+    hd.precision = (unsigned)h->precision;
+    hd.elem_bytes = (unsigned)eb;
+    hd.f_bytes = 2ull * lbfe::Q * N * eb;
+    hd.c_bytes = 6ull * N * sizeof(float);
+    hd.d_bytes = dens ? N * sizeof(float2) : 0ull;
+    std::vector<char> buf(hd.f_bytes + hd.c_bytes + hd.d_bytes);
+    char *fb = buf.data(), *cb = fb + hd.f_bytes, *db = cb + hd.c_bytes;
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaMemcpy2DAsync(fb, N * eb, I.f[h->cur], S * eb, N * eb, 2 * lbfe::Q, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpy2DAsync(cb, N * sizeof(float), I.C[h->cur], S * sizeof(float), N * sizeof(float), 6,
+                         cudaMemcpyDeviceToHost, h->stream));
+    // the state in f[cur] is stored relative to the offset densities dens[cur ^ 1]
+    if (dens) CK(cudaMemcpyAsync(db, I.dens[h->cur ^ 1], hd.d_bytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    hd.payload_crc = lbfe_crc32(buf.data(), buf.size(), 0);
+    hd.header_crc = header_crc(hd);
+    FileCloser fc{std::fopen(path, "wb")};
+    if (!fc.f) return LBFE_ERR_IO;
+    if (std::fwrite(&hd, sizeof hd, 1, fc.f) != 1) return LBFE_ERR_IO;
+    if (!buf.empty() && std::fwrite(buf.data(), buf.size(), 1, fc.f) != 1) return LBFE_ERR_IO;
+    const int rc = std::fclose(fc.f);
+    fc.f = nullptr;
+    return rc == 0 ? LBFE_OK : LBFE_ERR_IO;
+}
+
+lbfe_status lbfe_load(lbfe_handle *h, int k, const char *path) {
+    if (!h || !path || k < 0 || k >= h->n) return LBFE_ERR_BAD_PARAM;
+    InstDev &I = h->inst[k];
+    const size_t N = (size_t)I.N, S = (size_t)I.S, eb = elem_bytes(h->precision);
+    const bool dens = h->precision != LBFE_FP32 && I.dens[0] != nullptr;
+    FileCloser fc{std::fopen(path, "rb")};
+    if (!fc.f) return LBFE_ERR_IO;
+    CkptHeader hd{};
+    if (std::fread(&hd, sizeof hd, 1, fc.f) != 1) return LBFE_ERR_IO;
+    if (std::memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.version != 1 || hd.header_bytes != sizeof hd ||
+        hd.header_crc != header_crc(hd))
+        return LBFE_ERR_IO;
+    if (std::memcmp(&hd.params, &h->params[k], sizeof hd.params) != 0 || hd.cells != I.N ||
+        hd.precision != (unsigned)h->precision || hd.elem_bytes != eb)
+        return LBFE_ERR_BAD_PARAM;
+    if (hd.f_bytes != 2ull * lbfe::Q * N * eb || hd.c_bytes != 6ull * N * sizeof(float) ||
+        hd.d_bytes != (dens ? N * sizeof(float2) : 0ull))
+        return LBFE_ERR_IO;
+    std::vector<char> buf(hd.f_bytes + hd.c_bytes + hd.d_bytes);
+    if (!buf.empty() && std::fread(buf.data(), buf.size(), 1, fc.f) != 1) return LBFE_ERR_IO;
+    if (lbfe_crc32(buf.data(), buf.size(), 0) != hd.payload_crc) return LBFE_ERR_IO;
+    const char *fb = buf.data(), *cb = fb + hd.f_bytes, *db = cb + hd.c_bytes;
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaMemcpy2DAsync(I.f[h->cur], S * eb, fb, N * eb, N * eb, 2 * lbfe::Q, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpy2DAsync(I.C[h->cur], S * sizeof(float), cb, N * sizeof(float), N * sizeof(float), 6,
+                         cudaMemcpyHostToDevice, h->stream));
+    if (dens) CK(cudaMemcpyAsync(I.dens[h->cur ^ 1], db, hd.d_bytes, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemsetAsync(I.status, 0, sizeof(unsigned), h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->steps[k] = hd.steps;
+    h->ready[k] = 1;
     return LBFE_OK;
 }
 

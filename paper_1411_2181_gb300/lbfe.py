@@ -27,7 +27,7 @@ FIELD_F, FIELD_C, FIELD_RHO, FIELD_U = 0, 1, 2, 3
 STEP_CELL, STEP_PAIR = 0, 1   # lbfe_step_kernel
 INJECT_SHORT_COPIES = 1       # lbfe_test_inject
 
-OK, ERR_BAD_PARAM, ERR_NO_MEMORY, ERR_CUDA, ERR_DIVERGED, ERR_TIMEOUT, ERR_STATE = range(7)
+OK, ERR_BAD_PARAM, ERR_NO_MEMORY, ERR_CUDA, ERR_DIVERGED, ERR_TIMEOUT, ERR_STATE, ERR_IO = range(8)
 
 
 class CParams(ct.Structure):
@@ -77,6 +77,12 @@ _lib.lbfe_launch_config.argtypes = [_H] + [ct.POINTER(ct.c_int)] * 5
 _lib.lbfe_launch_config.restype = ct.c_int
 _lib.lbfe_test_inject.argtypes = [_H, ct.c_uint]
 _lib.lbfe_test_inject.restype = ct.c_int
+_lib.lbfe_save.argtypes = [_H, ct.c_int, ct.c_char_p]
+_lib.lbfe_save.restype = ct.c_int
+_lib.lbfe_load.argtypes = [_H, ct.c_int, ct.c_char_p]
+_lib.lbfe_load.restype = ct.c_int
+_lib.lbfe_crc32.argtypes = [ct.c_void_p, ct.c_size_t, ct.c_uint]
+_lib.lbfe_crc32.restype = ct.c_uint
 _lib.lbfe_observables_noalloc.argtypes = [_P, ct.c_void_p, ct.c_longlong, ct.POINTER(CObs), ct.c_void_p]
 _lib.lbfe_observables_noalloc.restype = ct.c_int
 for _fn in ("lbfe_derive", "lbfe_required_bytes", "lbfe_create", "lbfe_init", "lbfe_step",
@@ -207,6 +213,14 @@ class Solver:
 
     def check(self) -> int:
         return _lib.lbfe_check(self._h)
+
+    def save(self, k: int, path: str):
+        """Checkpoint instance k to a file (lbfe_save)."""
+        _check(_lib.lbfe_save(self._h, int(k), os.fsencode(path)), "lbfe_save")
+
+    def load(self, k: int, path: str):
+        """Resume instance k from a checkpoint written by save (lbfe_load)."""
+        _check(_lib.lbfe_load(self._h, int(k), os.fsencode(path)), "lbfe_load")
 
     def test_inject(self, what: int):
         """Test hook of the step kernel's failure path (lbfe_test_inject)."""

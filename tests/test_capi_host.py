@@ -83,3 +83,19 @@ def test_create_rejects_small_or_misaligned_block(lbfe):
 
 def test_test_inject_rejects_null_handle(lbfe):
     assert lbfe._lib.lbfe_test_inject(None, lbfe.INJECT_SHORT_COPIES) == lbfe.ERR_BAD_PARAM
+
+
+def test_crc32_known_answers(lbfe):
+    """CRC-32 check values of the reflected 0xEDB88320 polynomial: the
+    standard check string, the empty input, and continuation in pieces."""
+    crc = lbfe._lib.lbfe_crc32
+    s = b"123456789"
+    assert crc(s, len(s), 0) == 0xCBF43926
+    assert crc(b"", 0, 0) == 0
+    assert crc(s[4:], 5, crc(s, 4, 0)) == 0xCBF43926
+    assert crc(b"a", 1, 0) == 0xE8B7BE43
+
+
+def test_checkpoint_calls_reject_null_arguments(lbfe):
+    assert lbfe._lib.lbfe_save(None, 0, b"/nonexistent/x") == lbfe.ERR_BAD_PARAM
+    assert lbfe._lib.lbfe_load(None, 0, b"/nonexistent/x") == lbfe.ERR_BAD_PARAM
