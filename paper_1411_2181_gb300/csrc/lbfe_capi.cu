@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lbfe_internal.cuh"
 
 namespace lbfe {
@@ -41,6 +43,13 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 size_t elem_bytes(int precision) { return precision == LBFE_FP32 ? 4 : 2; }
+
+// NVTX range around a C-ABI call (visible in Nsight Systems / Compute
+// timelines; costs a branch when no tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 struct Derived {
     double nu_A, nu_B, pi_coef;
@@ -474,6 +483,7 @@ lbfe_status lbfe_create(lbfe_handle **hp, const lbfe_params *p, int n, void *dev
 }
 
 lbfe_status lbfe_init(lbfe_handle *h, int k, const double *rho_init) {
+    const NvtxRange nvtx_range("lbfe_init");
     if (!h || k < 0 || k >= h->n || !rho_init) return LBFE_ERR_BAD_PARAM;
     const InstDev &I = h->inst[k];
     // stage the densities (FP64) in the instance's scratch, then build f^eq
@@ -506,6 +516,7 @@ static cudaError_t build_step_graph(lbfe_handle *h, int cur) {
 }
 
 lbfe_status lbfe_step(lbfe_handle *h, long long nsteps) {
+    const NvtxRange nvtx_range("lbfe_step");
     if (!h || nsteps < 0) return LBFE_ERR_BAD_PARAM;
     for (int k = 0; k < h->n; ++k)
         if (!h->ready[k]) return LBFE_ERR_STATE;
@@ -539,6 +550,7 @@ lbfe_status lbfe_check(lbfe_handle *h) {
 }
 
 lbfe_status lbfe_observables(lbfe_handle *h, int k, lbfe_obs *out) {
+    const NvtxRange nvtx_range("lbfe_observables");
     if (!h || k < 0 || k >= h->n || !out) return LBFE_ERR_BAD_PARAM;
     if (!h->ready[k]) return LBFE_ERR_STATE;
     const InstDev &I = h->inst[k];
@@ -777,6 +789,7 @@ struct FileCloser {
 }  // namespace
 
 lbfe_status lbfe_save(lbfe_handle *h, int k, const char *path) {
+    const NvtxRange nvtx_range("lbfe_save");
     if (!h || !path || k < 0 || k >= h->n) return LBFE_ERR_BAD_PARAM;
     if (!h->ready[k]) return LBFE_ERR_STATE;
     const InstDev &I = h->inst[k];
@@ -815,6 +828,7 @@ lbfe_status lbfe_save(lbfe_handle *h, int k, const char *path) {
 }
 
 lbfe_status lbfe_load(lbfe_handle *h, int k, const char *path) {
+    const NvtxRange nvtx_range("lbfe_load");
     if (!h || !path || k < 0 || k >= h->n) return LBFE_ERR_BAD_PARAM;
     InstDev &I = h->inst[k];
     const size_t N = (size_t)I.N, S = (size_t)I.S, eb = elem_bytes(h->precision);

@@ -201,8 +201,8 @@ class Solver:
     def launches_per_step(self) -> int:
         return _lib.lbfe_launches_per_step(self._h)
 
-    def tune(self, tile_y: int = 16, z_chunk: int = 0, kernel: int = 0):
-        """Launch shape of the step: kernel STEP_CELL (tile_y in 4, 8, 16) or
+    def tune(self, tile_y: int = 8, z_chunk: int = 0, kernel: int = 0):
+        """Launch shape of the step: kernel STEP_CELL (tile_y in 8, 12, 16) or
         STEP_PAIR (tile_y 16, even Lx), and the z-chunk depth (0 = auto)."""
         _check(_lib.lbfe_tune(self._h, int(kernel), int(tile_y), int(z_chunk)), "lbfe_tune")
 
