@@ -99,6 +99,9 @@ typedef struct {
     double Ca;                /* eta_M gamma_dot R / sigma (Sec. 1) */
     double tau_em;            /* R eta_M / sigma, Eq. 9 */
     double De;                /* (tau_P / tau_em)(eta_P / eta_M), Eq. 8 */
+    double De_N1;             /* N1 R / (2 sigma Ca^2), Eq. 5, with the steady-shear
+                                 N1 of Eq. 7 at this shear rate; equals De in the
+                                 Oldroyd-B limit L^2 -> infinity */
 } lbfe_derived;
 
 /* Droplet observables of one instance. */

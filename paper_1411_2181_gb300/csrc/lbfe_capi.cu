@@ -375,6 +375,12 @@ lbfe_status lbfe_derive(const lbfe_params *p, lbfe_derived *out) {
         out->Ca = p->sigma > 0 ? p->eta_M * out->gamma_dot * p->R / p->sigma : 0.0;
         out->tau_em = p->sigma > 0 ? p->R * p->eta_M / p->sigma : 0.0;
         out->De = out->tau_em > 0 ? (p->tau_P / out->tau_em) * (p->eta_P / p->eta_M) : 0.0;
+        // Eq. 7: N1 = 8 (eta_P/tau_P)(L^2/6) sinh^2(asinh(gdot tau_P L^2/4 (L^2/6)^(-3/2)) / 3)
+        const double gd = std::fabs(out->gamma_dot), l6 = p->L2 / 6.0;
+        const double sh = std::sinh(std::asinh(gd * p->tau_P * p->L2 / 4.0 * std::pow(l6, -1.5)) / 3.0);
+        const double N1 = 8.0 * (p->eta_P / p->tau_P) * l6 * sh * sh;
+        const double Ca = std::fabs(out->Ca);
+        out->De_N1 = Ca > 0 ? N1 * p->R / (2.0 * p->sigma * Ca * Ca) : 0.0;
     }
     return LBFE_OK;
 }

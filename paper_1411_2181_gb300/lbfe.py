@@ -41,7 +41,7 @@ class CParams(ct.Structure):
 
 class CDerived(ct.Structure):
     _fields_ = [(n, ct.c_double) for n in
-                ("nu_A", "nu_B", "tau_A", "tau_B", "pi_coef", "gamma_dot", "Ca", "tau_em", "De")]
+                ("nu_A", "nu_B", "tau_A", "tau_B", "pi_coef", "gamma_dot", "Ca", "tau_em", "De", "De_N1")]
 
 
 class CObs(ct.Structure):

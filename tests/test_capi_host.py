@@ -99,3 +99,42 @@ def test_crc32_known_answers(lbfe):
 def test_checkpoint_calls_reject_null_arguments(lbfe):
     assert lbfe._lib.lbfe_save(None, 0, b"/nonexistent/x") == lbfe.ERR_BAD_PARAM
     assert lbfe._lib.lbfe_load(None, 0, b"/nonexistent/x") == lbfe.ERR_BAD_PARAM
+
+
+def test_deborah_number_from_n1(lbfe):
+    """Eq. 5 with the steady-shear N1 of Eq. 7 (De_N1) against Eq. 8 (De):
+    equal in the Oldroyd-B limit, and a few percent apart at L^2 = 100 in
+    the benchmark workload (the paper's estimate of the difference)."""
+    from dataclasses import replace
+    from paper_1411_2181_gb300 import configs
+    p, _, _ = configs.config2(0.2)
+    d = lbfe.derive(p)
+    assert 0.97 < d["De_N1"] / d["De"] < 1.0
+    big = lbfe.derive(replace(p, L2=1e10))
+    assert abs(big["De_N1"] / big["De"] - 1) < 1e-6
+
+
+def test_deborah_number_from_oracle_steady_shear(lbfe):
+    """De_N1 of the C ABI against N1 measured on the oracle: its FD FENE-P
+    update driven by the workload's shear rate to steady state, then
+    N1 = (eta_P/tau_P) f (C_xx - C_yy) in Eq. 5."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_1411_2181_gb300 import configs
+    p, _, _ = configs.config2(0.3)
+    d = lbfe.derive(p)
+    Lx, Ly, Lz = 1, 1, 2
+    gdot = d["gamma_dot"]
+    Uw = gdot * Lz / 2
+    q = dict(Lx=Lx, Ly=Ly, Lz=Lz, Uw=Uw, eta_M=1, tau_P=p.tau_P, L2=p.L2)
+    z = np.arange(Lz)
+    u = np.zeros((3, Lz, Ly, Lx))
+    u[0] = (Uw * (2 * (z + 0.5) / Lz - 1))[:, None, None]
+    C = np.zeros((6, Lz, Ly, Lx))
+    C[:3] = 1.0
+    for _ in range(int(40 * p.tau_P)):
+        C = O.fene_update(q, C, u)
+    f = (p.L2 - 3) / (p.L2 - (C[0] + C[1] + C[2]))
+    N1 = float((p.eta_P / p.tau_P) * (f * (C[0] - C[1])).mean())
+    De_num = N1 * p.R / (2 * p.sigma * d["Ca"] ** 2)
+    assert abs(De_num / d["De_N1"] - 1) < 1e-6
