@@ -82,6 +82,7 @@ typedef struct {
     double rho_in;        /* bulk density of a component where it is the majority */
     double rho_out;       /* bulk density of the dissolved (minority) component */
     double gx, gy, gz;    /* constant body acceleration (verification hook) */
+    int advection;        /* u.grad C: 0 first-order upwind, 1 second-order minmod-limited upwind */
 } orc_params;
 
 typedef struct {
@@ -282,9 +283,35 @@ static double C_at(const orc_params *p, const double *C, int k, int x, int y, in
     return C[(size_t)k * N + idx(p, wrap(x, p->Lx), wrap(y, p->Ly), clampz(z, p->Lz))];
 }
 
+/* minmod limiter: 0 where the two differences disagree in sign, else the
+ * one of smaller magnitude. */
+static double minmod(double a, double b) {
+    if (a * b <= 0.0) return 0.0;
+    return fabs(a) < fabs(b) ? a : b;
+}
+
+/* Second-order upwind derivative of component k along the unit vector e at
+ * (x, y, z) for a velocity component v (a reading: the paper defers its FD
+ * scheme).  With the limited slope s_j = minmod(C_{j+1} - C_j, C_j - C_{j-1})
+ * and face values reconstructed from the upwind side,
+ *   v > 0:  D = (C_0 + s_0/2) - (C_-1 + s_-1/2),
+ *   v <= 0: D = (C_1 - s_1/2) - (C_0 - s_0/2).
+ * Offsets past a wall take the wall cell's value (zero gradient, as for the
+ * first-order scheme); x and y are periodic. */
+static double d_upwind2(const orc_params *p, const double *C, int k, int x, int y, int z, const int e[3], double v) {
+    double c[5];
+    for (int j = -2; j <= 2; ++j) c[j + 2] = C_at(p, C, k, x + j * e[0], y + j * e[1], z + j * e[2]);
+    const double sm = minmod(c[2] - c[1], c[1] - c[0]);   /* slope at offset -1 */
+    const double s0 = minmod(c[3] - c[2], c[2] - c[1]);   /* slope at offset 0 */
+    const double sp = minmod(c[4] - c[3], c[3] - c[2]);   /* slope at offset +1 */
+    if (v > 0.0) return (c[2] + 0.5 * s0) - (c[1] + 0.5 * sm);
+    return (c[3] - 0.5 * sp) - (c[2] - 0.5 * s0);
+}
+
 /* FENE-P finite-difference update, Eq. 2 (and Eq. 4 for the matrix):
  * C^{n+1} = C + [ -u.grad C + C.(grad u) + (grad u)^T.C - (f C - I)/tau_P ]
- * with (grad u)_ij = d_i u_j (central), u.grad C first-order upwind, dt = 1. */
+ * with (grad u)_ij = d_i u_j (central), u.grad C upwind (first order, or
+ * second order with the minmod limiter when advection = 1), dt = 1. */
 void orc_fene_update(const orc_params *p, const double *C, const double *u, double *Cn) {
     size_t N = ncell(p);
     #pragma omp parallel for schedule(static)
@@ -310,7 +337,9 @@ void orc_fene_update(const orc_params *p, const double *C, const double *u, doub
                         double adv = 0.0;
                         for (int b = 0; b < 3; ++b) {
                             double c0 = Cm[i][j];
-                            if (uc[b] > 0.0) {
+                            if (p->advection == 1) {
+                                adv += uc[b] * d_upwind2(p, C, k, x, y, z, e[b], uc[b]);
+                            } else if (uc[b] > 0.0) {
                                 double cm = C_at(p, C, k, x - e[b][0], y - e[b][1], z - e[b][2]);
                                 adv += uc[b] * (c0 - cm);
                             } else {

@@ -37,7 +37,7 @@ class Params(ct.Structure):
                 ("Uw", ct.c_double), ("G", ct.c_double), ("eta_M", ct.c_double),
                 ("lambda_", ct.c_double), ("eta_P", ct.c_double), ("tau_P", ct.c_double),
                 ("L2", ct.c_double), ("rho_in", ct.c_double), ("rho_out", ct.c_double),
-                ("gx", ct.c_double), ("gy", ct.c_double), ("gz", ct.c_double)]
+                ("gx", ct.c_double), ("gy", ct.c_double), ("gz", ct.c_double), ("advection", ct.c_int)]
 
 
 class Obs(ct.Structure):
@@ -98,6 +98,7 @@ def make_params(d: dict) -> Params:
     p.rho_out = float(d.get("rho_out", 0.0))
     g = d.get("g", (0.0, 0.0, 0.0))
     p.gx, p.gy, p.gz = float(g[0]), float(g[1]), float(g[2])
+    p.advection = int(d.get("advection", 0))
     return p
 
 
