@@ -70,11 +70,20 @@ typedef enum {
 } lbfe_visco_phase;
 
 /* Parameters of one droplet instance (lattice units). */
+/* Discretisation of u . grad C in the FENE-P update (the paper defers its
+ * FD scheme).  UPWIND1: first-order upwind.  UPWIND2_MINMOD: second-order
+ * upwind with minmod-limited slopes (face values reconstructed from the
+ * upwind side); runs with the one-cell step kernel at 8-row tiles only. */
+typedef enum {
+    LBFE_ADVECTION_UPWIND1 = 0,
+    LBFE_ADVECTION_UPWIND2_MINMOD = 1
+} lbfe_advection;
+
 typedef struct {
     int Lx, Ly, Lz;           /* lattice; the wall gap W is Lz */
     int visco_phase;          /* lbfe_visco_phase */
     int precision;            /* lbfe_precision (the same for every instance of a batch) */
-    int reserved0;
+    int advection;            /* lbfe_advection of u.grad C (the same for every instance of a batch) */
     double R;                 /* droplet radius at rest: reference length of L_p/2R and Ca */
     double Uw;                /* wall speed; shear rate 2 Uw / W */
     double G;                 /* Shan-Chen inter-component coupling (> 0 separates) */
@@ -197,8 +206,10 @@ typedef enum {
 /* Launch shape of the step kernel: variant (lbfe_step_kernel), column-tile
  * height tile_y (tile width 32; 16 for LBFE_STEP_PAIR) and z-chunk depth in
  * planes (0 = automatic: fill the resident blocks of the GPU about once).
- * A new handle starts with LBFE_STEP_CELL, tile_y 8 (FP32) or 12 (FP16 /
- * BF16 storage) and the automatic z-chunk.
+ * A new handle starts with LBFE_STEP_CELL, tile_y 8 (FP32, or any precision
+ * with LBFE_ADVECTION_UPWIND2_MINMOD) or 12 (FP16 / BF16 storage) and the
+ * automatic z-chunk.  With LBFE_ADVECTION_UPWIND2_MINMOD only
+ * LBFE_STEP_CELL at tile_y 8 is accepted.
  * LBFE_ERR_BAD_PARAM for an unsupported combination.  Synchronises the
  * stream. */
 lbfe_status lbfe_tune(lbfe_handle *h, int step_kernel, int tile_y, int z_chunk);

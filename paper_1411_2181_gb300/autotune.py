@@ -25,7 +25,7 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "auto
 
 def _key(params: list[Params], gpu: str) -> str:
     dims = ";".join(f"{p.Lx}x{p.Ly}x{p.Lz}" for p in params)
-    return f"{gpu}|v2|prec{params[0].precision}|n{len(params)}|{dims}"
+    return f"{gpu}|v2|prec{params[0].precision}|adv{params[0].advection}|n{len(params)}|{dims}"
 
 
 def _load(path):
@@ -38,11 +38,15 @@ def _load(path):
 
 def candidates(params: list[Params]):
     """(kernel, tile_y, z_chunk) triples: cell kernel (0) at every tile
-    height, pair kernel (1) at 16 rows when every Lx is even."""
+    height, pair kernel (1) at 16 rows when every Lx is even; with the
+    second-order advection scheme the cell kernel at 8 rows only."""
     lz = max(p.Lz for p in params)
-    shapes = [(0, ty) for ty in TILE_Y]
-    if all(p.Lx % 2 == 0 for p in params):
-        shapes.append((1, 16))
+    if params[0].advection:
+        shapes = [(0, 8)]        # the second-order advection runs at 8-row tiles only
+    else:
+        shapes = [(0, ty) for ty in TILE_Y]
+        if all(p.Lx % 2 == 0 for p in params):
+            shapes.append((1, 16))
     return [(k, ty, zc) for k, ty in shapes for zc in Z_CHUNKS if zc <= lz]
 
 

@@ -69,6 +69,7 @@ lbfe_status derive(const lbfe_params &p, Derived &d) {
     if (!(p.tau_P > 0.0) || !(p.L2 > 3.0) || !(p.rho_in > 0.0) || !(p.rho_out >= 0.0)) return LBFE_ERR_BAD_PARAM;
     if (!(std::fabs(p.Uw) < 0.1) || !(p.eta_M > 0.0) || !(p.lambda > 0.0) || !(p.eta_P >= 0.0)) return LBFE_ERR_BAD_PARAM;
     if (!(p.G >= 0.0)) return LBFE_ERR_BAD_PARAM;
+    if (p.advection != LBFE_ADVECTION_UPWIND1 && p.advection != LBFE_ADVECTION_UPWIND2_MINMOD) return LBFE_ERR_BAD_PARAM;
     const double rho_ref = p.rho_in + p.rho_out;
     const double eta_d = p.lambda * p.eta_M;
     double eta_A = eta_d, eta_B = p.eta_M;
@@ -229,6 +230,7 @@ struct lbfe_handle {
     lbfe::StepMaps *maps_dev = nullptr;
     int total_items = 0, fused_grid = 0, tile_y = 16, z_chunk_req = 0, num_sms = 0, blocks_per_sm = 0;
     int step_kernel = LBFE_STEP_CELL;
+    int advection = 0;               // lbfe_params::advection of every instance
     unsigned inject = 0;             // lbfe_test_inject bits
     unsigned *status = nullptr;
     double *mass = nullptr;
@@ -266,6 +268,7 @@ struct lbfe_handle {
         c.fused_grid = fused_grid;
         c.tile_y = tile_y;
         c.step_kernel = step_kernel;
+        c.advection = advection;
         return c;
     }
 };
@@ -283,8 +286,10 @@ static lbfe_status configure_fused(lbfe_handle *h, int step_kernel, int tile_y, 
         return LBFE_ERR_BAD_PARAM;
     }
     if (z_chunk < 0) return LBFE_ERR_BAD_PARAM;
+    // the second-order advection scheme has the one-cell kernel at 8 rows only
+    if (h->advection != 0 && (step_kernel != LBFE_STEP_CELL || tile_y != 8)) return LBFE_ERR_BAD_PARAM;
     int bps = 0;
-    cudaError_t e = lbfe::fused_prepare(step_kernel, tile_y, h->precision, &bps);
+    cudaError_t e = lbfe::fused_prepare(step_kernel, tile_y, h->precision, h->advection, &bps);
     if (e != cudaSuccess) return cuda_fail(e, "fused_prepare");
     if (bps < 1) return LBFE_ERR_BAD_PARAM;
     long long columns = 0;
@@ -390,7 +395,7 @@ lbfe_status lbfe_required_bytes(const lbfe_params *p, int n, size_t *bytes) {
     for (int k = 0; k < n; ++k) {
         lbfe_status s = lbfe_derive(p + k, nullptr);
         if (s != LBFE_OK) return s;
-        if (p[k].precision != p[0].precision) return LBFE_ERR_BAD_PARAM;
+        if (p[k].precision != p[0].precision || p[k].advection != p[0].advection) return LBFE_ERR_BAD_PARAM;
     }
     *bytes = plan(p, n).total;
     return LBFE_OK;
@@ -409,6 +414,7 @@ lbfe_status lbfe_create(lbfe_handle **hp, const lbfe_params *p, int n, void *dev
     if (!h) return LBFE_ERR_NO_MEMORY;
     h->n = n;
     h->precision = p[0].precision;
+    h->advection = p[0].advection;
     h->stream = (cudaStream_t)stream;
     h->params.assign(p, p + n);
     h->steps.assign(n, 0);
@@ -479,7 +485,8 @@ lbfe_status lbfe_create(lbfe_handle **hp, const lbfe_params *p, int n, void *dev
     }
     // default shape: the one the autotuner picks for the 192 x 96 x 80
     // workload on most GB300s (8-row tiles in FP32, 12-row with 2-byte storage)
-    lbfe_status st = configure_fused(h, LBFE_STEP_CELL, h->precision == LBFE_FP32 ? 8 : 12, 0);
+    lbfe_status st =
+        configure_fused(h, LBFE_STEP_CELL, (h->precision == LBFE_FP32 || h->advection != 0) ? 8 : 12, 0);
     if (st != LBFE_OK) {
         delete h;
         return st;

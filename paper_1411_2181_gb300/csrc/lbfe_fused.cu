@@ -9,7 +9,7 @@
 
 namespace lbfe {
 
-template <typename T, int TY>
+template <typename T, int TY, bool ADV2 = false>
 __global__ void __launch_bounds__(32 * TY, 1)
 k_fused(const __grid_constant__ StepArgs A) {
     using Gm = Geom<TY>;
@@ -138,6 +138,7 @@ k_fused(const __grid_constant__ StepArgs A) {
         // this thread has a halo cell staged in the region copy
         const bool staged_halo = St::REGION && tma && h_on[0] && h_dom[0];
         float FA[3], FB[3], uo[3], rAo = 1.f, rBo = 0.f;
+        float cprev[6];   // second-order advection: own C of plane r - 2 (see stage_u_cell)
 
         for (int p = z0 - 2; p <= z1 + 1; ++p) {
             const int q = p - 1, r = p - 2;
@@ -199,6 +200,10 @@ k_fused(const __grid_constant__ StepArgs A) {
                     // done with the staging buffer (early issue reads the staged
                     // halo cell before the own cell)
                     if (kEarlyIssue) mbar_arrive(ebar);
+                    if constexpr (ADV2) {
+                        if (p == z0 - 2)
+                            for (int q6 = 0; q6 < 6; ++q6) cprev[q6] = m.c[q6];
+                    }
                     m_store<TY>(I, m, idx_in, L.r3[2], ring2(p), L.cf[2]);
                     tm_store38(tm_warp + (u32)((p & 1) * 64), reinterpret_cast<const float *>(m.ab));
                 }
@@ -314,7 +319,7 @@ k_fused(const __grid_constant__ StepArgs A) {
             // stage F: threads without halo work in stage F go on to it.
             if (r >= z0 && r < z1 && valid) {
                 float cn[6];
-                if (!stage_u_cell<TY>(I, idx_in, L, r, cn)) raise_step_flag(A.status, I, kFlagDiverged);
+                if (!stage_u_cell<TY, ADV2>(I, idx_in, L, r, cn, cprev)) raise_step_flag(A.status, I, kFlagDiverged);
                 const u32 n = (u32)(r * LxLy) + ofs_in;
 #pragma unroll
                 for (int q6 = 0; q6 < 6; ++q6) Cout[(u32)(q6 * S + n)] = cn[q6];
@@ -403,27 +408,29 @@ EncodeTiledFn encode_tiled() {
     return fn;
 }
 
-template <typename T, int TY>
+template <typename T, int TY, bool ADV2>
 cudaError_t cell_launch_t(const StepArgs &a, int grid, cudaStream_t st) {
-    k_fused<T, TY><<<grid, Geom<TY>::NT, smem_bytes<T, TY>(), st>>>(a);
+    k_fused<T, TY, ADV2><<<grid, Geom<TY>::NT, smem_bytes<T, TY>(), st>>>(a);
     return cudaGetLastError();
 }
 
-template <int TY>
+template <int TY, bool ADV2 = false>
 cudaError_t cell_launch_ty(const StepArgs &a, int grid, int precision, cudaStream_t st) {
     switch (precision) {
-        case LBFE_FP16_OFFSET: return cell_launch_t<__half, TY>(a, grid, st);
-        case LBFE_BF16_OFFSET: return cell_launch_t<__nv_bfloat16, TY>(a, grid, st);
-        default: return cell_launch_t<float, TY>(a, grid, st);
+        case LBFE_FP16_OFFSET: return cell_launch_t<__half, TY, ADV2>(a, grid, st);
+        case LBFE_BF16_OFFSET: return cell_launch_t<__nv_bfloat16, TY, ADV2>(a, grid, st);
+        default: return cell_launch_t<float, TY, ADV2>(a, grid, st);
     }
 }
 
-template <typename T, int TY>
+template <typename T, int TY, bool ADV2>
 cudaError_t prep_t(int *bps) {
     const size_t smem = smem_bytes<T, TY>();
-    cudaError_t e = cudaFuncSetAttribute(k_fused<T, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_fused<T, TY, ADV2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int b = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fused<T, TY>, Geom<TY>::NT, smem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fused<T, TY, ADV2>, Geom<TY>::NT, smem);
     if (e != cudaSuccess) return e;
     // resident blocks of one SM share its 512 TMEM columns
     const int tm = 512 / Geom<TY>::TMEM_COLS;
@@ -431,12 +438,12 @@ cudaError_t prep_t(int *bps) {
     return cudaSuccess;
 }
 
-template <int TY>
+template <int TY, bool ADV2 = false>
 cudaError_t prep_ty(int precision, int *bps) {
     switch (precision) {
-        case LBFE_FP16_OFFSET: return prep_t<__half, TY>(bps);
-        case LBFE_BF16_OFFSET: return prep_t<__nv_bfloat16, TY>(bps);
-        default: return prep_t<float, TY>(bps);
+        case LBFE_FP16_OFFSET: return prep_t<__half, TY, ADV2>(bps);
+        case LBFE_BF16_OFFSET: return prep_t<__nv_bfloat16, TY, ADV2>(bps);
+        default: return prep_t<float, TY, ADV2>(bps);
     }
 }
 
@@ -457,12 +464,15 @@ cudaError_t fused_group(const LaunchCtx &c, int cur, int k0, int k1) {
     if (a.total_items <= 0) return cudaSuccess;
     const int grid = a.total_items < c.fused_slots ? a.total_items : c.fused_slots;
     if (c.step_kernel == LBFE_STEP_PAIR) return step_pair_launch(a, grid, c.precision, c.stream);
-    return step_cell_launch(a, grid, c.tile_y, c.precision, c.stream);
+    return step_cell_launch(a, grid, c.tile_y, c.precision, c.advection, c.stream);
 }
 
 }  // namespace
 
-cudaError_t step_cell_launch(const StepArgs &a, int grid, int tile_y, int precision, cudaStream_t st) {
+cudaError_t step_cell_launch(const StepArgs &a, int grid, int tile_y, int precision, int advection,
+                             cudaStream_t st) {
+    // the second-order advection scheme runs at 8-row tiles only
+    if (advection == 1) return cell_launch_ty<8, true>(a, grid, precision, st);
     switch (tile_y) {
         case 12: return cell_launch_ty<12>(a, grid, precision, st);
         case 16: return cell_launch_ty<16>(a, grid, precision, st);
@@ -470,7 +480,8 @@ cudaError_t step_cell_launch(const StepArgs &a, int grid, int tile_y, int precis
     }
 }
 
-cudaError_t step_cell_prepare(int tile_y, int precision, int *blocks_per_sm) {
+cudaError_t step_cell_prepare(int tile_y, int precision, int advection, int *blocks_per_sm) {
+    if (advection == 1) return prep_ty<8, true>(precision, blocks_per_sm);
     switch (tile_y) {
         case 12: return prep_ty<12>(precision, blocks_per_sm);
         case 16: return prep_ty<16>(precision, blocks_per_sm);
@@ -539,9 +550,9 @@ cudaError_t fused_pop_maps(const InstDev &I, int precision, int tile_y, bool sho
     return cudaSuccess;
 }
 
-cudaError_t fused_prepare(int step_kernel, int tile_y, int precision, int *blocks_per_sm) {
+cudaError_t fused_prepare(int step_kernel, int tile_y, int precision, int advection, int *blocks_per_sm) {
     if (step_kernel == LBFE_STEP_PAIR) return step_pair_prepare(precision, blocks_per_sm);
-    return step_cell_prepare(tile_y, precision, blocks_per_sm);
+    return step_cell_prepare(tile_y, precision, advection, blocks_per_sm);
 }
 
 }  // namespace lbfe

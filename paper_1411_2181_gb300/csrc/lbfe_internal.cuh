@@ -146,6 +146,7 @@ struct LaunchCtx {
     const int *item_off_host;        // host copy of item_off
     int total_items, fused_grid, tile_y;
     int step_kernel;                 // lbfe_step_kernel
+    int advection = 0;               // lbfe_params::advection of the batch
     int fused_slots;                 // resident blocks of the fused kernel on the GPU
     const struct PopMaps *maps_host; // per instance: TMA maps of the step kernel (may be null)
     const struct StepMaps *maps_dev; // device copies, [instance][parity]
@@ -172,7 +173,7 @@ cudaError_t launch_fused(const LaunchCtx &c, int cur);
 // Kernel launches of one time step of n instances.
 int fused_launches(int n);
 // Resident blocks per SM of the fused kernel for a tile height.
-cudaError_t fused_prepare(int step_kernel, int tile_y, int precision, int *blocks_per_sm);
+cudaError_t fused_prepare(int step_kernel, int tile_y, int precision, int advection, int *blocks_per_sm);
 cudaError_t launch_moments(const LaunchCtx &c, int cur);
 cudaError_t launch_forces(const LaunchCtx &c, int cur);
 cudaError_t launch_init(const LaunchCtx &c, int k, const double *rho_dev, int cur);

@@ -101,8 +101,9 @@ struct StepArgs {
 };
 
 // Kernel launchers (one launch over the instances of one StepArgs).
-cudaError_t step_cell_launch(const StepArgs &a, int grid, int tile_y, int precision, cudaStream_t st);
-cudaError_t step_cell_prepare(int tile_y, int precision, int *blocks_per_sm);
+cudaError_t step_cell_launch(const StepArgs &a, int grid, int tile_y, int precision, int advection,
+                             cudaStream_t st);
+cudaError_t step_cell_prepare(int tile_y, int precision, int advection, int *blocks_per_sm);
 cudaError_t step_pair_launch(const StepArgs &a, int grid, int precision, cudaStream_t st);
 cudaError_t step_pair_prepare(int precision, int *blocks_per_sm);
 
@@ -616,12 +617,26 @@ __device__ __forceinline__ void stage_f_cell(const StepInst &I, int idx, const S
     Rg::uz(L.r3[1])[idx] = u[2];
 }
 
+__device__ __forceinline__ float minmodf(float a, float b) {
+    if (a * b <= 0.f) return 0.f;
+    return fabsf(a) < fabsf(b) ? a : b;
+}
+
 // Stage U for one cell (ring index idx) of plane r: the FENE-P update of
 // Eq. 2 (Eq. 4) with central grad u (u_ghost = 2 U_wall - u at the walls)
 // and first-order upwind u . grad C (C mirrored at the walls).  Writes the
 // new conformation to cn; returns false when tr C reached L^2.
-template <int TY>
-__device__ __forceinline__ bool stage_u_cell(const StepInst &I, int idx, const Slots &L, int r, float cn[6]) {
+// ADV2: u . grad C by the second-order minmod-limited upwind scheme instead
+// of the first-order one.  Along an axis with speed |v|, upwind neighbour a,
+// the next one aa and the downwind neighbour b, the contribution is
+//   |v| [(c - a) + (minmod(b - c, c - a) - minmod(c - a, a - aa)) / 2],
+// the difference of the two face values reconstructed from the upwind side
+// (the same for either sign of v).  z needs C of plane r - 2, which the ring
+// no longer holds: cprev carries the cell's own C of that plane from the
+// previous call (and is updated to plane r - 1 here).
+template <int TY, bool ADV2 = false>
+__device__ __forceinline__ bool stage_u_cell(const StepInst &I, int idx, const Slots &L, int r, float cn[6],
+                                             float *cprev = nullptr) {
     constexpr int RX = Geom<TY>::RX;
     using Rg = Ring<TY>;
     const float Uw = I.Uw;
@@ -654,19 +669,45 @@ __device__ __forceinline__ bool stage_u_cell(const StepInst &I, int idx, const S
         const float2 p0 = Rg::c(s, 0)[n], p1 = Rg::c(s, 1)[n], p2 = Rg::c(s, 2)[n];
         out[0] = p0.x; out[1] = p1.x; out[2] = p2.y; out[3] = p0.y; out[4] = p2.x; out[5] = p1.y;
     };
-    float c[6], cx_[6], cy_[6], cz6[6];
+    float c[6];
     c_at(L.cu[1], idx, c);
-    // first-order upwind u . grad C (C mirrored at the walls)
+    // upwind u . grad C (C mirrored at the walls)
     const int ox = u0[0] > 0.f ? -1 : 1, oy = u0[1] > 0.f ? -RX : RX;
     const float sx = u0[0] > 0.f ? u0[0] : -u0[0], sy = u0[1] > 0.f ? u0[1] : -u0[1];
     const float sz = u0[2] > 0.f ? u0[2] : -u0[2];
-    c_at(L.cu[1], idx + ox, cx_);
-    c_at(L.cu[1], idx + oy, cy_);
-    c_at(u0[2] > 0.f ? L.cu[0] : L.cu[2], idx, cz6);
     float adv[6];
+    if constexpr (!ADV2) {
+        float cx_[6], cy_[6], cz6[6];
+        c_at(L.cu[1], idx + ox, cx_);
+        c_at(L.cu[1], idx + oy, cy_);
+        c_at(u0[2] > 0.f ? L.cu[0] : L.cu[2], idx, cz6);
 #pragma unroll
-    for (int q6 = 0; q6 < 6; ++q6)
-        adv[q6] = sx * (c[q6] - cx_[q6]) + sy * (c[q6] - cy_[q6]) + sz * (c[q6] - cz6[q6]);
+        for (int q6 = 0; q6 < 6; ++q6)
+            adv[q6] = sx * (c[q6] - cx_[q6]) + sy * (c[q6] - cy_[q6]) + sz * (c[q6] - cz6[q6]);
+    } else {
+        float xa[6], xaa[6], xb[6], ya[6], yaa[6], yb[6], zm1[6], zp1[6], zp2[6];
+        c_at(L.cu[1], idx + ox, xa);
+        c_at(L.cu[1], idx + 2 * ox, xaa);
+        c_at(L.cu[1], idx - ox, xb);
+        c_at(L.cu[1], idx + oy, ya);
+        c_at(L.cu[1], idx + 2 * oy, yaa);
+        c_at(L.cu[1], idx - oy, yb);
+        c_at(L.cu[0], idx, zm1);    // plane r - 1
+        c_at(L.cu[2], idx, zp1);    // plane r + 1
+        c_at(L.cf[2], idx, zp2);    // plane r + 2
+        const bool zup = u0[2] > 0.f;
+        auto lim = [](float c0, float a, float aa, float b) {
+            return (c0 - a) + 0.5f * (minmodf(b - c0, c0 - a) - minmodf(c0 - a, a - aa));
+        };
+#pragma unroll
+        for (int q6 = 0; q6 < 6; ++q6) {
+            const float za = zup ? zm1[q6] : zp1[q6], zaa = zup ? cprev[q6] : zp2[q6], zb = zup ? zp1[q6] : zm1[q6];
+            adv[q6] = sx * lim(c[q6], xa[q6], xaa[q6], xb[q6]) + sy * lim(c[q6], ya[q6], yaa[q6], yb[q6]) +
+                      sz * lim(c[q6], za, zaa, zb);
+        }
+#pragma unroll
+        for (int q6 = 0; q6 < 6; ++q6) cprev[q6] = zm1[q6];
+    }
     const float Cm[3][3] = {{c[0], c[3], c[4]}, {c[3], c[1], c[5]}, {c[4], c[5], c[2]}};
     const float fp = peterlin(I.L2, c[0], c[1], c[2]);
 #pragma unroll

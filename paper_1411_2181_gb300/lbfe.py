@@ -13,7 +13,8 @@ from dataclasses import asdict
 
 import numpy as np
 
-from .params import Params, FP32, FP16_OFFSET, BF16_OFFSET, NEWTONIAN, DROPLET_VISCOELASTIC, MATRIX_VISCOELASTIC
+from .params import (Params, FP32, FP16_OFFSET, BF16_OFFSET, NEWTONIAN, DROPLET_VISCOELASTIC, MATRIX_VISCOELASTIC,
+                     ADVECTION_UPWIND1, ADVECTION_UPWIND2_MINMOD)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "liblbfe.so")
@@ -32,7 +33,7 @@ OK, ERR_BAD_PARAM, ERR_NO_MEMORY, ERR_CUDA, ERR_DIVERGED, ERR_TIMEOUT, ERR_STATE
 
 class CParams(ct.Structure):
     _fields_ = [("Lx", ct.c_int), ("Ly", ct.c_int), ("Lz", ct.c_int), ("visco_phase", ct.c_int),
-                ("precision", ct.c_int), ("reserved0", ct.c_int),
+                ("precision", ct.c_int), ("advection", ct.c_int),
                 ("R", ct.c_double), ("Uw", ct.c_double), ("G", ct.c_double), ("eta_M", ct.c_double),
                 ("lambda_", ct.c_double), ("eta_P", ct.c_double), ("tau_P", ct.c_double),
                 ("L2", ct.c_double), ("rho_in", ct.c_double), ("rho_out", ct.c_double),

@@ -6,6 +6,7 @@ from dataclasses import dataclass
 
 FP32, FP16_OFFSET, BF16_OFFSET = 0, 1, 2
 NEWTONIAN, DROPLET_VISCOELASTIC, MATRIX_VISCOELASTIC = 0, 1, 2
+ADVECTION_UPWIND1, ADVECTION_UPWIND2_MINMOD = 0, 1
 
 
 @dataclass
@@ -29,13 +30,14 @@ class Params:
     g: tuple = (0.0, 0.0, 0.0)
     precision: int = FP32
     rho0: tuple = (0.0, 0.0)
+    advection: int = ADVECTION_UPWIND1
 
     def oracle_dict(self) -> dict:
         """The same parameters as the plain dict the CPU oracle takes."""
         return dict(Lx=self.Lx, Ly=self.Ly, Lz=self.Lz, visco_phase=self.visco_phase, Uw=self.Uw,
                     G=self.G, eta_M=self.eta_M, **{"lambda": self.lambda_}, eta_P=self.eta_P,
                     tau_P=self.tau_P, L2=self.L2, rho_in=self.rho_in, rho_out=self.rho_out,
-                    g=tuple(self.g))
+                    g=tuple(self.g), advection=self.advection)
 
     @property
     def N(self) -> int:

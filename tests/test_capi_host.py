@@ -138,3 +138,17 @@ def test_deborah_number_from_oracle_steady_shear(lbfe):
     N1 = float((p.eta_P / p.tau_P) * (f * (C[0] - C[1])).mean())
     De_num = N1 * p.R / (2 * p.sigma * d["Ca"] ** 2)
     assert abs(De_num / d["De_N1"] - 1) < 1e-6
+
+
+def test_advection_scheme_validation(lbfe):
+    from dataclasses import replace
+    from paper_1411_2181_gb300 import configs
+    p, _, _ = configs.config1()
+    assert lbfe.derive(replace(p, advection=1))["Ca"] > 0
+    import pytest as _pt
+    with _pt.raises(lbfe.LbfeError) as ei:
+        lbfe.derive(replace(p, advection=2))
+    assert ei.value.status == lbfe.ERR_BAD_PARAM
+    with _pt.raises(lbfe.LbfeError) as ei:
+        lbfe.required_bytes([p, replace(p, advection=1)])
+    assert ei.value.status == lbfe.ERR_BAD_PARAM
