@@ -43,7 +43,13 @@ def main(argv=None):
     ap.add_argument("--out", default=None)
     ap.add_argument("--params-out", default=None)
     ap.add_argument("--params-in", default=None, help="reuse a trained network (skips the training runs)")
+    ap.add_argument("--trend", action="store_true",
+                    help="only Ca_cr by bisection against the confinement 2R/W for Newtonian, DV and MV "
+                         "droplets at De = 2, lambda = 1 (the trends of Figs. 2 and 4, reduced domains)")
+    ap.add_argument("--trend-lambda", type=float, default=1.0, help="viscosity ratio of the --trend cases")
     a = ap.parse_args(argv)
+    if a.trend:
+        return trend(a.out, a.trend_lambda)
 
     report = {}
     t0 = time.perf_counter()
@@ -93,6 +99,32 @@ def main(argv=None):
     print(txt)
     if a.out:
         with open(a.out, "w") as fh:
+            fh.write(txt)
+    return report
+
+
+def trend(out=None, lam=1.0):
+    """Ca_cr (bisection, bracket width 0.02) for Newtonian (De = 0), droplet-
+    and matrix-viscoelastic (De = 2) droplets at viscosity ratio lam and 2R/W in
+    {0.6, 0.7, 0.8} on the study's reduced domains.  Sec. 3 reports, at the
+    paper's sizes, that confinement raises Ca_cr, droplet viscoelasticity
+    raises it further and matrix viscoelasticity lowers it."""
+    kinds = (("newtonian", 0.0, 1), ("DV", 2.0, 1), ("MV", 2.0, 2))
+    confs = (0.6, 0.7, 0.8)
+    triples = [(De, lam, conf, phase) for conf in confs for _, De, phase in kinds]
+    t0 = time.perf_counter()
+    sb, st = study.search_bisect(triples)
+    rows = {}
+    for (name, _, _), i in zip(kinds * len(confs), range(len(triples))):
+        s = sb[i]
+        rows.setdefault(name, []).append({"2R/W": s.triple[2], "Ca_cr": 0.5 * (s.lo + s.hi),
+                                          "bracket": [s.lo, s.hi], "runs": s.runs})
+    report = {"lambda": lam, "trend": rows, "runs": st.get("runs", 0), "rounds": st.get("rounds", 0),
+              "diverged": st.get("diverged", 0), "seconds": time.perf_counter() - t0}
+    txt = json.dumps(report, indent=1)
+    print(txt)
+    if out:
+        with open(out, "w") as fh:
             fh.write(txt)
     return report
 
