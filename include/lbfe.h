@@ -223,9 +223,11 @@ lbfe_status lbfe_launch_config(const lbfe_handle *h, int *step_kernel, int *tile
  * paper).  what = LBFE_INJECT_SHORT_COPIES: the TMA tensor maps of the
  * populations are rebuilt with boxes one row short of what the step kernel
  * expects, so that the completion barrier of each block's first copy never
- * completes.  The block's bounded wait expires (after about one second of
- * GPU time), the whole block stops before issuing another copy, waits once
- * more (bounded) for the copy's barrier, frees its tensor memory and exits;
+ * completes.  Each thread's bounded wait expires (after about one second of
+ * GPU time); from then on it waits for no copy and the block's issuing
+ * thread issues none, the block runs through its work items on stale data
+ * (the step's result is invalid), waits once more (bounded) for the barrier
+ * of the last copy it issued, frees its tensor memory and exits;
  * lbfe_check then reports LBFE_ERR_TIMEOUT (the launch status word keeps the
  * flag for the life of the handle).  Only instances whose staging uses TMA
  * (Lx * element size a multiple of 16 bytes) wait.  what = 0 restores the
