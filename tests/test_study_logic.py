@@ -92,3 +92,22 @@ def test_range_ends_need_one_run_when_predicted(fake_runs):
     searches, _ = study.search_mlp(TRIPLES, FakeNetwork(5.0), tol=0.02, delta=0.06, hi=1.0)
     for s in searches:
         assert s.lo == s.hi == 1.0 and s.runs == 1
+
+
+def test_autotune_candidates():
+    """Launch shapes the autotuner tries: every tile height of the one-cell
+    kernel, the two-cell kernel only when every Lx is even, and only 8-row
+    tiles with the second-order advection scheme; z-chunks no deeper than
+    the deepest instance."""
+    from dataclasses import replace
+    from paper_1411_2181_gb300 import autotune
+    from paper_1411_2181_gb300.params import Params
+    p = Params(Lx=64, Ly=32, Lz=24)
+    shapes = {(k, ty) for k, ty, _ in autotune.candidates([p])}
+    assert shapes == {(0, 8), (0, 12), (0, 16), (1, 16)}
+    assert all(zc <= 24 for _, _, zc in autotune.candidates([p]))
+    odd = {(k, ty) for k, ty, _ in autotune.candidates([p, replace(p, Lx=63)])}
+    assert (1, 16) not in odd
+    adv = {(k, ty) for k, ty, _ in autotune.candidates([replace(p, advection=1)])}
+    assert adv == {(0, 8)}
+    assert autotune._key([p], "gpu") != autotune._key([replace(p, advection=1)], "gpu")
