@@ -32,11 +32,22 @@
  *     F_P = div Pi by central differences;
  *   C^{n+1} = C + [-u.grad C (first-order upwind) + C.grad u + (grad u)^T.C
  *     - (f C - I)/tau_P], (grad u)_ij = d_i u_j by central differences;
+ *     optionally (advection = 1) u.grad C by second-order upwind with
+ *     minmod-limited slopes;
  *   FD ghosts at the walls: C and rho mirrored, u_ghost = 2 U_wall - u;
  *   halfway bounce-back with the moving-wall momentum term.
  * One step performs, over full fields and in this order: moments, Shan-Chen
  * force, polymer stress and its divergence, velocity, FENE-P update,
  * collision, streaming.  The LB force uses C^n; C^{n+1} uses u^n.
+ *
+ * Pins (tests/test_oracle_*.py): Couette and Poiseuille solutions, exact
+ * mass conservation, the Guo moment identities, closed forms of the
+ * Shan-Chen and polymer forces, flat-interface coexistence and the Laplace
+ * law, Eqs. 6 and 7 in steady shear, the Oldroyd-B start-up, the stencils'
+ * exact properties (including the second-order advection on quadratics and
+ * its boundedness), and the observables on built shapes.  The coupled
+ * droplet dynamics as a whole have no closed form: parity unpinned beyond
+ * these pins.
  *
  * Layout (shared interface format, restated independently on the GPU side):
  *   cell index n = (z*Ly + y)*Lx + x;
