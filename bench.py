@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--advection", choices=["upwind1", "upwind2"], default="upwind1",
                     help="u.grad C scheme: first-order upwind, or second-order minmod-limited upwind")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the sub-records of the other storage forms, config 3 and the 64-instance batch")
+    ap.add_argument("--_oracle-timing", dest="oracle_timing", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -192,28 +195,59 @@ def profiled_traffic(workload_name: str, precision: int):
 
 
 # ---------------------------------------------------------------- CPU oracle
-def oracle_sample(p, rho, budget_s=12.0, max_steps=None):
-    """Time the FP64 oracle (as it stands) on a z-slab of the workload box:
-    the full x-y plane, depth chosen so one step takes about 1 s."""
+def oracle_timing_child(spec: str):
+    """Run in a child process (its OpenMP thread count fixed by the
+    environment): time the FP64 oracle, as it stands, on one case and print
+    one JSON line."""
     import numpy as np
     from oracle import oracle as O
-    O.build()
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    d = p.oracle_dict()
-    # probe a thin slab to estimate the rate, then size the sample
-    dz = max(4, min(p.Lz, 8))
-    d2 = dict(d, Lz=dz)
-    o = O.Oracle(d2, np.ascontiguousarray(rho[:, :dz]))
-    t = time.perf_counter(); o.step(1); rate = p.Lx * p.Ly * dz / (time.perf_counter() - t)
-    dz = int(max(4, min(p.Lz, rate * 1.0 / (p.Lx * p.Ly))))
-    steps = int(max(2, min(max_steps or 10 ** 9, budget_s * rate / (p.Lx * p.Ly * dz))))
-    d3 = dict(d, Lz=dz)
-    o = O.Oracle(d3, np.ascontiguousarray(rho[:, :dz]))
-    t = time.perf_counter(); o.step(steps); dt = time.perf_counter() - t
-    mlups = p.Lx * p.Ly * dz * steps / dt / 1e6
-    return {"value": round(mlups, 4), "unit": METRIC, "cores": cores, "kind": "oracle",
-            "sample": f"{steps} FP64 oracle steps on a {p.Lx}x{p.Ly}x{dz} slab of the workload "
-                      f"(walls at both ends), {dt:.1f} s, OpenMP threads={cores}"}
+    d = json.loads(spec)
+    ps, rhos = workload(d["workload"], 0)
+    p, rho = ps[0], rhos[0]
+    dz = min(p.Lz, int(d["planes"])) if d.get("planes") else p.Lz
+    o = O.Oracle(dict(p.oracle_dict(), Lz=dz), np.ascontiguousarray(rho[:, :dz]))
+    o.step(1)
+    t = time.perf_counter()
+    o.step(int(d["steps"]))
+    dt = time.perf_counter() - t
+    print(json.dumps({"mlups": p.Lx * p.Ly * dz * int(d["steps"]) / dt / 1e6, "seconds": dt,
+                      "lattice": [p.Lx, p.Ly, dz]}))
+
+
+def oracle_timings(cores: int):
+    """The FP64 oracle on the host cores, single-threaded and on all cores:
+    config 1 (32^3, 500 steps) and a 200-step slice of config 2 (the full
+    192 x 96 plane over a z-slab of the box; a single thread takes about a
+    minute per million cells, so the slab keeps that leg to seconds)."""
+    cases = [("box_32cubed", 500, None), ("matrix_ve_192x96x80", 200, 4)]
+    out = []
+    for name, steps, planes in cases:
+        for threads in (1, cores):
+            env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+            spec = json.dumps({"workload": name, "steps": steps, "planes": planes})
+            r = subprocess.run([sys.executable, os.path.abspath(__file__), "--_oracle-timing", spec],
+                               capture_output=True, text=True, env=env, timeout=900)
+            if r.returncode != 0:
+                out.append({"workload": name, "threads": threads, "error": r.stderr.strip()[-300:]})
+                continue
+            d = json.loads(r.stdout.strip().splitlines()[-1])
+            out.append({"workload": name, "steps": steps, "lattice": d["lattice"], "threads": threads,
+                        "value": round(d["mlups"], 4), "unit": METRIC, "seconds": round(d["seconds"], 2)})
+    return out
+
+
+def cpu_baseline_record():
+    """cpu_baseline of the JSON line: the all-core config-2 slice as the
+    headline value, with all four timings beside it."""
+    cores = os.cpu_count() or 1
+    runs = oracle_timings(cores)
+    head = next((r for r in runs if r.get("workload") == "matrix_ve_192x96x80" and r.get("threads") == cores
+                 and "value" in r), None)
+    return {"value": head["value"] if head else None, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": ("FP64 oracle as it stands, OpenMP threads = 1 and = all host cores: config 1 "
+                       "(32^3, 500 steps) and 200 steps of config 2 on its full 192 x 96 plane over a "
+                       "4-plane z-slab (walls at both ends); value = the all-core config-2 slice"),
+            "runs": runs}
 
 
 # ---------------------------------------------------------------- ours
@@ -235,6 +269,79 @@ def whole_job_mlups(cells_per_rank: int, steps: int, t_max_ms: float, world: int
     return cells_per_rank * steps / (t_max_ms / 1e3) / 1e6 * world
 
 
+def timed_steps(s, stream, steps: int, warmup: int, dist=False):
+    """Warm-up, then `steps` steps bracketed by CUDA events on the solver's
+    stream (barrier + synchronize on both sides); returns ms."""
+    import torch
+    for _ in range(warmup):
+        s.step(1)
+    torch.cuda.synchronize()
+    if dist:
+        import torch.distributed as tdist
+        tdist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    s.step(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1)
+
+
+def roofline_record(prec: int, ncell: int, ms_per_step: float, workload_name: str, advection: int):
+    peak, peak_kind = measured_peak()
+    algo = ALGO_BYTES[prec]
+    achieved = algo * ncell / (ms_per_step / 1e3) / 1e9
+    # the committed summaries are of the default (first-order) step kernel
+    traffic_per_lup, prof_file = (profiled_traffic(workload_name, prec) if advection == 0 else (None, None))
+    return {"bound": "hbm", "kernel": "k_fused (whole time step in one kernel)",
+            "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "algorithmic_bytes_per_lup": algo,
+            "traffic": (round(traffic_per_lup * ncell) if traffic_per_lup else None),
+            "traffic_source": os.path.relpath(prof_file, ROOT) if (prof_file and traffic_per_lup) else None}
+
+
+def time_form(name: str, prec: int, steps: int, warmup: int, device: str, autotune_on: bool):
+    """One sub-record: the workload `name` in storage form `prec`, autotuned,
+    timed on its own stream with CUDA events (state resident in HBM)."""
+    import torch
+    from paper_1411_2181_gb300 import lbfe, autotune
+    ps, rhos = workload(name, prec)
+    ncell = sum(p.N for p in ps)
+    shape = autotune.tune(ps, device=device, rho=rhos) if autotune_on else None
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = lbfe.Solver(ps, device=device, stream=stream)
+        if shape:
+            s.tune(shape["tile_y"], shape["z_chunk"], shape.get("kernel", 0))
+        for k, r in enumerate(rhos):
+            s.init(k, r)
+        ms = timed_steps(s, stream, steps, warmup)
+        st = s.check()
+        launch = s.launch_config()
+        s.close()
+    del s
+    torch.cuda.empty_cache()
+    msps = ms / steps
+    roof = roofline_record(prec, ncell, msps, name, 0)
+    return {"workload": name, "dtype": DTYPE[prec], "cells": ncell, "steps": steps,
+            "value": round(ncell * steps / (ms / 1e3) / 1e6, 2), "unit": METRIC, "ms_per_step": round(msps, 5),
+            "roofline": {k: roof[k] for k in ("achieved", "peak", "unit", "frac", "algorithmic_bytes_per_lup",
+                                              "traffic")},
+            "launch": launch, "status": lbfe._lib.lbfe_status_str(st).decode()}
+
+
+# the other forms of the metric: FP16 / BF16 storage beside FP32 on the
+# headline lattice, the strongly confined 256 x 128 x 64 droplet in all three
+# forms, and the 64-instance uneven batch in one persistent launch per step
+FORMS = [("matrix_ve_192x96x80", 1), ("matrix_ve_192x96x80", 2),
+         ("droplet_ve_256x128x64", 0), ("droplet_ve_256x128x64", 1), ("droplet_ve_256x128x64", 2),
+         ("batched_64", 0)]
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -253,7 +360,8 @@ def run_ours(a):
         tdist.barrier()
     from paper_1411_2181_gb300 import lbfe, autotune
     prec = {"fp32": 0, "fp16": 1, "bf16": 2}[a.precision]
-    ps, rhos = workload(a.workload, prec, 1 if a.advection == "upwind2" else 0)
+    adv = 1 if a.advection == "upwind2" else 0
+    ps, rhos = workload(a.workload, prec, adv)
     ncell = sum(p.N for p in ps)
     shape = None
     if not a.no_autotune:
@@ -265,24 +373,13 @@ def run_ours(a):
             s.tune(shape["tile_y"], shape["z_chunk"], shape.get("kernel", 0))
         for k, r in enumerate(rhos):
             s.init(k, r)
-        for _ in range(a.warmup):
-            s.step(1)
-        torch.cuda.synchronize()
-        if dist:
-            tdist.barrier()
-        torch.cuda.synchronize()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with ClockSampler(local) as clk:
-            ev0.record(stream)
-            s.step(a.steps)
-            ev1.record(stream)
-            torch.cuda.synchronize()
-        if dist:
-            tdist.barrier()
-        torch.cuda.synchronize()
-        ms = ev0.elapsed_time(ev1)
+            ms = timed_steps(s, stream, a.steps, a.warmup, dist)
         st = s.check()
         launch = s.launch_config()
+        launches = s.launches_per_step() * a.steps
+        status = lbfe._lib.lbfe_status_str(st).decode()
+        s.close()
     t_max = reduce_max_ms(ms, device=f"cuda:{local}")
     ms_per_step = t_max / a.steps
     value = whole_job_mlups(ncell, a.steps, t_max, world)
@@ -314,22 +411,28 @@ def run_ours(a):
                "h2d_bytes_per_step": int(sum(h.numel() for h in hosts) * 8 / a.steps),
                "d2h_bytes_per_step": int(obs_bytes / a.steps),
                "timed": "lbfe_init (pinned H2D of rho[2][N] float64) + lbfe_step(K) + lbfe_observables"}
+    torch.cuda.empty_cache()
 
-    peak, peak_kind = measured_peak()
-    algo = ALGO_BYTES[prec]
-    achieved = algo * ncell / (ms_per_step / 1e3) / 1e9
-    # the committed summaries are of the default (first-order) step kernel
-    traffic_per_lup, prof_file = (profiled_traffic(a.workload, prec) if a.advection == "upwind1"
-                                  else (None, None))
-    roof = {"bound": "hbm", "kernel": "k_fused (whole time step in one kernel)",
-            "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "algorithmic_bytes_per_lup": algo,
-            "traffic": (round(traffic_per_lup * ncell) if traffic_per_lup else None),
-            "traffic_source": os.path.relpath(prof_file, ROOT) if (prof_file and traffic_per_lup) else None}
+    roof = roofline_record(prec, ncell, ms_per_step, a.workload, adv)
+
+    # the other forms, each timed on its own (one GPU only: the scaling runs
+    # time the headline alone)
+    forms = None
+    if not a.no_forms and world == 1 and a.workload == "matrix_ve_192x96x80" and adv == 0:
+        forms = []
+        for name, fprec in FORMS:
+            if (name, fprec) == (a.workload, prec):
+                continue
+            fsteps = max(3, a.steps // 20) if name == "batched_64" else a.steps
+            try:
+                forms.append(time_form(name, fprec, fsteps, max(3, a.warmup), f"cuda:{local}",
+                                       not a.no_autotune))
+            except Exception as e:   # recorded, not fatal: the headline stands on its own
+                forms.append({"workload": name, "dtype": DTYPE[fprec], "error": str(e)[:300]})
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        cpu = oracle_sample(ps[0], rhos[0])
+        cpu = cpu_baseline_record()
 
     if rank == 0:
         out = {"metric": METRIC, "value": round(value, 2), "unit": METRIC, "n_gpus": world,
@@ -337,9 +440,9 @@ def run_ours(a):
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": DTYPE[prec], "data": "synthetic (seeded droplet, NumPy PCG64)",
                "config": dict(config_dict(a.workload, ps), launch=launch), "roofline": roof, "cpu_baseline": cpu,
-               "e2e": e2e, "clocks": clk.summary(), "gpu_launches": s.launches_per_step() * a.steps,
-               "autotune": autotune_summary(shape),
-               "status": lbfe._lib.lbfe_status_str(st).decode(),
+               "e2e": e2e, "clocks": clk.summary(), "gpu_launches": launches,
+               "autotune": autotune_summary(shape), "forms": forms,
+               "status": status,
                "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
         print(json.dumps(out))
     if dist:
@@ -399,7 +502,9 @@ def run_reference(a):
 
 if __name__ == "__main__":
     args = parse()
-    if args.impl == "reference":
+    if args.oracle_timing:
+        oracle_timing_child(args.oracle_timing)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -170,7 +170,12 @@ lbfe_status lbfe_create(lbfe_handle **h, const lbfe_params *p, int n, void *devi
  * start).  Resets the step counter.  Copies synchronously from host memory. */
 lbfe_status lbfe_init(lbfe_handle *h, int k, const double *rho_init);
 
-/* Advance every instance by nsteps time steps (asynchronous on the stream).
+/* Advance every instance by nsteps time steps of the hybrid scheme (Sec. 2:
+ * the two-component lattice-Boltzmann collide + stream with the Shan-Chen
+ * force, the per-site relaxation time of the viscosity ratio and the
+ * moving walls of Sec. 3, coupled to the finite-difference FENE-P update of
+ * C (Eqs. 2 and 4) and to the polymer-stress divergence of Eqs. 1 and 3),
+ * asynchronously on the stream.
  * With nsteps >= 2 the steps replay CUDA graphs of one step (captured once
  * per launch shape on a private stream); results are identical to single
  * steps.  Inside a stream capture of the caller the kernels are launched
@@ -245,14 +250,21 @@ lbfe_status lbfe_test_inject(lbfe_handle *h, unsigned what);
  *   p       parameters of the field (sizes, precision, storage offsets rho0;
  *           validated as in lbfe_derive);
  *   f_dev   device pointer to populations [2][19][stride] in the storage
- *           type of p->precision, in the layout and order of this header;
+ *           type of p->precision, in the layout and order of this header.
+ *           FP32: the populations themselves.  FP16 / BF16: f_i - w_i rho0_s
+ *           with the CONSTANT offsets p->rho0[s]; the solver's own reduced
+ *           state is stored against per-cell offset densities instead and
+ *           cannot be decoded here (use lbfe_observables for it, or pass
+ *           its FP32 populations from lbfe_get_field);
  *   stride  elements between population arrays, >= Lx*Ly*Lz;
  *   out     host result (same fields and readings as lbfe_observables;
  *           step and t_over_tem are 0);
  *   stream  cudaStream_t or NULL; synchronised before return.
  * Scratch lives in a file-scope device array of about 200 KB that every
- * GPU loading the library keeps until the process exits, so Lx is limited
- * to 4096: larger Lx returns LBFE_ERR_BAD_PARAM before any device work.
+ * GPU loading the library keeps until the process exits.  It holds the
+ * per-plane sums of up to 4096 x-planes, which covers every Lx that
+ * lbfe_derive accepts (larger Lx returns LBFE_ERR_BAD_PARAM from that
+ * validation, before any device work).
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) and caches it; make that first call before any
  * stream capture.  Every call shares the array and it keeps the last

@@ -92,6 +92,7 @@ __device__ __forceinline__ void raise_flag(unsigned *global, const InstDev &I, u
 }
 
 constexpr int kBlock = 256;          // threads per block of the cell-per-thread kernels
+constexpr int kMaxLx = 4096;         // largest Lx lbfe_derive accepts
 constexpr int kObsBlocks = 304;      // 2 x 152 SMs for the observables reduction
 
 __device__ __forceinline__ int wrapi(int a, int L) { return a < 0 ? a + L : (a >= L ? a - L : a); }
@@ -180,5 +181,11 @@ cudaError_t launch_init(const LaunchCtx &c, int k, const double *rho_dev, int cu
 cudaError_t launch_decode_pop(const LaunchCtx &c, int k, int cur, int s, int i, float *dst);
 cudaError_t launch_encode_pop(const LaunchCtx &c, int k, int cur, int s, int i, const float *src);
 cudaError_t launch_observables(const LaunchCtx &c, int k, int cur, double *mass_out_dev);
+
+// Host-side droplet analysis (lbfe_analysis.cu): from the observables
+// kernel's per-plane sums prof[6][Lx], fill L_p, L_p/2R, necks, fragments,
+// broken, volume, centroid, M, D and theta of out.
+void droplet_from_profile(const unsigned long long *prof, int Lx, double R, lbfe_obs *out);
+void sym_eig3(const double M[6], double ev[3], double V[3][3]);
 
 }  // namespace lbfe

@@ -832,11 +832,17 @@ __device__ __forceinline__ void collide_push_ab(const float2 *fv, T *__restrict_
 
 // Called by every block once it has taken its last item: the last block to
 // finish returns the two counters to zero for the next launch (no other
-// block reads them any more).
+// block reads them any more).  The fence orders the block's last fetch on
+// work[0] before its arrival on work[1], so the last arriver's reset comes
+// after every other block's final fetch; the reset itself is atomic and
+// fenced before the kernel ends.
 __device__ __forceinline__ void release_work_counters(unsigned *work) {
+    __threadfence();
     if (atomicAdd(work + 1, 1u) == gridDim.x - 1) {
-        work[0] = 0u;
-        work[1] = 0u;
+        __threadfence();
+        atomicExch(work, 0u);
+        atomicExch(work + 1, 0u);
+        __threadfence();
     }
 }
 

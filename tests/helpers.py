@@ -47,3 +47,18 @@ def component_report(gpu: np.ndarray, ref: np.ndarray) -> str:
     r = ref.reshape(ref.shape[0], -1)
     return "; ".join(f"k{k}: |d|max={np.abs(g[k]-r[k]).max():.2e} |ref|max={np.abs(r[k]).max():.2e}"
                      for k in range(g.shape[0]))
+
+
+C_NAMES = ("xx", "yy", "zz", "xy", "xz", "yz")
+
+
+def component_errors(gpu: np.ndarray, ref: np.ndarray) -> dict:
+    """Per conformation component k: (max |C_gpu,k - C_ref,k| / max |C_ref,k|,
+    max |C_ref,k|), each component normalised by its own scale."""
+    g = gpu.reshape(6, -1).astype(np.float64)
+    r = ref.reshape(6, -1)
+    out = {}
+    for k, name in enumerate(C_NAMES):
+        scale = float(np.abs(r[k]).max())
+        out[name] = (float(np.abs(g[k] - r[k]).max() / scale) if scale > 0 else 0.0, scale)
+    return out

@@ -6,7 +6,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_1411_2181_gb300 import configs, synth
-from tests.helpers import component_report, norm_err, random_populations, tensor_err
+from tests.helpers import component_errors, component_report, norm_err, random_populations, tensor_err
 
 pytestmark = pytest.mark.gpu
 
@@ -63,6 +63,13 @@ def test_config1_parity_500_steps(L, kernel):
     eC = tensor_err(C, orc.C)
     print(f"config1 500 steps: f {ef:.3e}, C {eC:.3e};", component_report(C, orc.C))
     assert ef < TOL_500 and eC < TOL_500, (ef, eC, component_report(C, orc.C))
+    # each conformation component against its own scale (every component
+    # whose reference scale exceeds 1e-3; all six do here, the shear
+    # component C_xz included)
+    per = component_errors(C, orc.C)
+    checked = {k: e for k, (e, scale) in per.items() if scale > 1e-3}
+    assert {"xx", "zz", "xz"} <= set(checked), per
+    assert max(checked.values()) < TOL_500, per
     assert s.check() == L.OK
 
 

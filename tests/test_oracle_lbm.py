@@ -1,10 +1,25 @@
 """Pins of the oracle's lattice-Boltzmann part against closed forms,
 conservation laws and textbook results (no GPU)."""
+import os
+
 import numpy as np
 import pytest
 
 from oracle import oracle as O
 from paper_1411_2181_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "shan_chen_constants.txt")
+
+
+def golden_sigma(name: str) -> float:
+    """Interfacial tension of a Laplace entry of the golden fixture (fitted
+    on static cylinders by the oracle-only fixture script)."""
+    with open(GOLDEN) as fh:
+        for line in fh:
+            w = line.split()
+            if len(w) > 7 and w[0] == "laplace" and w[1] == name:
+                return float(w[7])
+    raise KeyError(name)
 
 CX = np.array([0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0])
 CY = np.array([0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1])
@@ -249,3 +264,30 @@ def test_laplace_law_cylinder():
     assert sigma > 0
     assert r2 > 0.999
     assert abs(icpt) < 0.15 * dp.max()
+
+
+def test_laplace_law_sphere_3d():
+    """Static spherical droplets (three-dimensional Laplace law, Sec. 2's
+    Shan-Chen interface): p_in - p_out = 2 sigma / R, with p the Shan-Chen
+    pressure of test_laplace_law_cylinder and R the equal-volume radius of
+    the relaxed droplet.  The sigma it gives matches, within 5%, the sigma
+    the cylinders fit with p_in - p_out = sigma / R (the tabulated G = 3.1
+    value): the factor 2 of the sphere's two principal curvatures, with the
+    same interfacial tension."""
+    G = 3.1
+    sigma_cyl = golden_sigma("laplace_G3.1")
+    for R, L in ((8, 36), (10, 40)):
+        p = dict(Lx=L, Ly=L, Lz=L, Uw=0.0, G=G, eta_M=1.04 / 6, rho_in=1.0, rho_out=0.04)
+        o = O.Oracle(p, synth.droplet_densities(L, L, L, R, noise=0.0, center_offset=False))
+        o.step(1200)
+        r = o.detail()["rho"]
+        P = (r[0] + r[1]) / 3 + G / 3 * r[0] * r[1]
+        c = L // 2
+        a_in, a_out = r[0, c, c, c], r[0, c, 0, 0]
+        V = ((r[0] - a_out) / (a_in - a_out)).sum()
+        R_eq = (3 * V / (4 * np.pi)) ** (1 / 3)
+        dp = P[c, c, c] - P[c, 0, 0]
+        sigma = dp * R_eq / 2
+        assert abs(sigma / sigma_cyl - 1) < 0.05, (R, R_eq, dp, sigma, sigma_cyl)
+        # a cylinder's law (one curvature) would be off by a factor 2
+        assert abs(dp * R_eq / sigma_cyl - 1) > 0.8
