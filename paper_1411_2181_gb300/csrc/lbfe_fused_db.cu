@@ -449,27 +449,39 @@ k_fused_db(const __grid_constant__ StepArgs A) {
                     plane = Po.z0 - 2 + (p + d - (z1 + 2));
                     return true;
                 };
+                // the conformation first: the next stage M needs it, and the
+                // copies queued on an SM complete in the order issued
                 ItemPos Po;
                 int plane;
-                if (ahead(NB, Po, plane) && A.inst[Po.k].tma) {
-                    issue_pop_db<T>(A, Po, plane, pbuf0 + pb * St::PBUF, smem_addr(&s_pbar[pb]), go);
-                    pany |= go << pb;
-                    pcnt ^= go << pb;
-                }
                 if (ahead(1, Po, plane) && A.inst[Po.k].tma) {
                     issue_c_db(A, Po, plane, cbuf, cbar, go);
                     cany |= go;
                     ccnt ^= go;
                 }
+                if (ahead(NB, Po, plane) && A.inst[Po.k].tma) {
+                    issue_pop_db<T>(A, Po, plane, pbuf0 + pb * St::PBUF, smem_addr(&s_pbar[pb]), go);
+                    pany |= go << pb;
+                    pcnt ^= go << pb;
+                }
             }
-            const bool doX = q >= z0 && q < z1;
-            u32 tr[38];
+            // the collision's populations and stage U's own-cell values of
+            // plane r - 1 start to come back from TMEM here, ahead of stage F
+            const bool doX = q >= z0 && q < z1, doU = r >= z0 && r < z1;
+            u32 tr[38], hv[9];
+            if (doX || doU) tm_wait_st();
             if (doX) {
                 const u32 ta = tm_warp + (u32)((q & 1) * 64);
-                tm_wait_st();
                 tm_ld32(ta, tr);
                 tm_ld4(ta + 32, tr + 32);
                 tm_ld2(ta + 36, tr + 36);
+            }
+            if (doU) {
+                const u32 tc = tm_warp + kTmC + (u32)(((r - 1) & 3) * 8);
+                const u32 tu = tm_warp + kTmU + (u32)(((r - 1) & 3) * 4);
+                tm_ld4(tc, hv);
+                tm_ld2(tc + 4, hv + 4);
+                tm_ld2(tu, hv + 6);
+                tm_ld1(tu + 2, hv + 8);
             }
             // ---------------- stage F(q): radius-1 region
             if (q >= max(z0 - 1, 0) && q <= min(z1, Lz - 1)) {
@@ -518,15 +530,7 @@ k_fused_db(const __grid_constant__ StepArgs A) {
                 }
             }
             // ---------------- stage U(r): FENE-P update
-            if (r >= z0 && r < z1) {
-                u32 hv[9];
-                const u32 tc = tm_warp + kTmC + (u32)(((r - 1) & 3) * 8);
-                const u32 tu = tm_warp + kTmU + (u32)(((r - 1) & 3) * 4);
-                tm_wait_st();
-                tm_ld4(tc, hv);
-                tm_ld2(tc + 4, hv + 4);
-                tm_ld2(tu, hv + 6);
-                tm_ld1(tu + 2, hv + 8);
+            if (doU) {
                 tm_wait_ld9(hv);
                 if (valid) {
                     const float cm[6] = {__uint_as_float(hv[0]), __uint_as_float(hv[1]), __uint_as_float(hv[2]),
