@@ -305,6 +305,8 @@ k_fused_db(const __grid_constant__ StepArgs A) {
     __shared__ u32 s_tmem;
     __shared__ __align__(8) unsigned long long s_pbar[NB];   // population buffers filled
     __shared__ __align__(8) unsigned long long s_cbar;       // conformation buffer filled
+    // every thread has read what it needs from the staging buffers (NT arrivals per plane)
+    __shared__ __align__(8) unsigned long long s_empty;
     __shared__ int s_item[2];
 
     const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
@@ -314,7 +316,15 @@ k_fused_db(const __grid_constant__ StepArgs A) {
     const u32 cbuf = pbuf0 + (u32)NB * St::PBUF;
     const char *gen0 = reinterpret_cast<const char *>(lbfe_smem4) - smem_base;   // generic = gen0 + shared address
     const float *stage_c = reinterpret_cast<const float *>(gen0 + cbuf);
-    const u32 cbar = smem_addr(&s_cbar);
+    const u32 cbar = smem_addr(&s_cbar), ebar = smem_addr(&s_empty);
+    // The copies are issued by lane 0 of the last warp, which has no halo
+    // cells in stage M: as soon as every thread has read its cells from the
+    // staging buffers it starts the next copies (an issue can stall while
+    // the SM's copy engine is busy with the copy in flight; that thread has
+    // the slack to absorb it), before the stage-M barrier.
+    constexpr int kIssuer = NT - 32;
+    static_assert(kIssuer >= Gm::NRING2 && kIssuer >= Gm::NRING1, "the issuing warp has no halo cells");
+    u32 eparity = 0;     // issuer: phase parity of the next buffers-read phase
     // phase parities of the next completion waited for, per barrier
     u32 ppar = 0;        // bit b: population buffer b
     u32 cpar = 0;
@@ -329,6 +339,7 @@ k_fused_db(const __grid_constant__ StepArgs A) {
 #pragma unroll
         for (int b = 0; b < NB; ++b) mbar_init(smem_addr(&s_pbar[b]));
         mbar_init(cbar);
+        mbar_init_count(ebar, NT);
     }
     tm_fence_before();
     __syncthreads();
@@ -338,8 +349,8 @@ k_fused_db(const __grid_constant__ StepArgs A) {
     // Block b starts with item b; further items from the launch's counter,
     // one ahead.  Plane loads are numbered per block across its items; load
     // k uses population buffer k % NB.
-    if (t == 0) {
-        s_item[0] = blockIdx.x;
+    if (t == 0) s_item[0] = blockIdx.x;
+    if (t == kIssuer) {
         if ((int)blockIdx.x < A.total_items) {
             const ItemPos P0 = item_pos<TY>(A, blockIdx.x);
             if (A.inst[P0.k].tma) {
@@ -412,12 +423,16 @@ k_fused_db(const __grid_constant__ StepArgs A) {
                     if (!expired && !mbar_wait(cbar, cpar)) expired = true;
                     cpar ^= 1u;
                 }
+                // the staged halo cell first, then the own cell: every thread is
+                // then done with the staging buffers
+                if (h_on && tma && h_dom) m_load_region_db<T>(I, stage, stage_c, h_gx, h_gy, pl + h_ofs, mh);
                 {
                     MCell m;
                     if (tma && valid)
                         m_load_region_db<T>(I, stage, stage_c, tx + 2, ty + 2, pl + ofs_in, m);
                     else
                         m_load<T>(I, fin, Cin, S, pl + ofs_in, m);
+                    mbar_arrive(ebar);
                     m_store_db(I, m, idx_in, s3[2]);
                     tm_store38(tm_warp + (u32)((p & 1) * 64), reinterpret_cast<const float *>(m.ab));
                     // own C of plane p, for stage U(p + 1)
@@ -425,14 +440,11 @@ k_fused_db(const __grid_constant__ StepArgs A) {
                     tm_st4(tc, m.c);
                     tm_st2(tc + 4, m.c + 4);
                 }
-                if (h_on) {
-                    if (tma && h_dom) m_load_region_db<T>(I, stage, stage_c, h_gx, h_gy, pl + h_ofs, mh);
-                    m_store_db(I, mh, h_idx, s3[2]);
-                }
+                if (h_on) m_store_db(I, mh, h_idx, s3[2]);
             }
-            __syncthreads();
-            if (t == 0) {
-                if (p == z0 - 2) s_item[slot ^ 1] = next_t0;
+            if (t == kIssuer) {
+                if (!expired && !mbar_wait(ebar, eparity)) expired = true;
+                eparity ^= 1u;
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 const u32 go = expired ? 0u : 1u;
                 // population load kload + NB into the buffer just read; the
@@ -443,7 +455,8 @@ k_fused_db(const __grid_constant__ StepArgs A) {
                         plane = p + d;
                         return true;
                     }
-                    const int nx = next_t0;   // this thread took it at the item's start
+                    // published at the item's first plane (at least three planes ago)
+                    const int nx = s_item[slot ^ 1];
                     if (nx >= A.total_items) return false;
                     Po = item_pos<TY>(A, nx);
                     plane = Po.z0 - 2 + (p + d - (z1 + 2));
@@ -464,6 +477,8 @@ k_fused_db(const __grid_constant__ StepArgs A) {
                     pcnt ^= go << pb;
                 }
             }
+            __syncthreads();
+            if (t == 0 && p == z0 - 2) s_item[slot ^ 1] = next_t0;
             // the collision's populations and stage U's own-cell values of
             // plane r - 1 start to come back from TMEM here, ahead of stage F
             const bool doX = q >= z0 && q < z1, doU = r >= z0 && r < z1;
@@ -551,7 +566,7 @@ k_fused_db(const __grid_constant__ StepArgs A) {
     }
 
     if (t == 0 && A.total_items > (int)gridDim.x) release_work_counters(A.work);
-    if (expired && t == 0) {
+    if (expired && t == kIssuer) {
         // copies issued but not waited for may still be in flight: wait,
         // bounded, for the last phase of each barrier before the block's
         // shared memory is released
