@@ -1,21 +1,26 @@
 // lbfe_fused_db.cu -- the time step with one cell per thread on 32 x 8
-// tiles and the plane copies pipelined NB planes deep (NB = 2 for FP32
-// storage, 3 for the 2-byte forms).
+// tiles and the plane copies pipelined two planes deep.
 //
 // The arithmetic is that of k_fused (lbfe_fused.cu, stages described in
-// lbfe_step.cuh); what differs is where the planes wait:
-//  * NB staging buffers for the populations (and, in the reduced forms,
-//    the offset densities) of the radius-2 region: the copy of plane p + NB
-//    starts once stage M has read plane p, so NB copies are in flight while
-//    the block works, instead of one;
-//  * one staging buffer for the conformation box, copied one plane ahead;
-//  * to make room, the rings hold three planes each: the momentum j of
-//    plane p shares the velocity ring (F(q) turns the slot's j(q) into
-//    u(q) in place), and the two values that fell out of the rings -- the
-//    own cell's C of plane r - 1 and u of plane r - 1 for stage U(r) --
-//    wait in tensor memory (per-thread lanes, like the populations of the
-//    collision), written by stages M and F and read back by stage U.
-// Shared memory for FP32: rings 67.4 KB + 2 x 73.0 KB + 11.5 KB = 225 KB.
+// lbfe_step.cuh); what differs is where the planes wait.  With one staging
+// buffer the copy of plane p + 1 can only start once stage M has read plane
+// p, and the copy's latency (about 2 us for the 85 KB region of an 8-row
+// tile) is then exposed on every plane together with the step's own global
+// writes.  Here two staging buffers each take a whole plane (populations,
+// the conformation box and, in the reduced forms, the offset densities), so
+// the copy of plane p + 2 is in flight while planes p and p + 1 are worked
+// on.  To make room (FP32: 2 x 84.5 KB of staging):
+//  * the rings hold three planes each: the momentum j of plane p shares the
+//    velocity ring (F(q) turns the slot's j(q) into u(q) in place), and the
+//    two values that fell out -- the own cell's C and u of plane r - 1 for
+//    stage U(r) -- wait in tensor memory (per-thread lanes, like the
+//    populations of the collision), written by stages M and F and read back
+//    by stage U;
+//  * there is no ring of stress scalars: stage F evaluates the prefactor
+//    a f and a of Pi = a (f C) - a I at the six face neighbours from the
+//    density and conformation rings (the same expression stage M of k_fused
+//    stores).
+// Shared memory for FP32: rings 57.0 KB + 2 x 82.5 KB = 226 KB.
 #include "lbfe_step.cuh"
 
 namespace lbfe {
@@ -24,47 +29,44 @@ namespace {
 
 constexpr int DTY = 8;   // tile height of this kernel
 
-// Rings (offsets in floats): rho float2 [3][R2N]; pi float2 [3][R2N];
-// C [3] x float2 [3][R2N] ((xx, xy), (yy, yz), (xz, zz)); uj [3] x
-// (float2 [R2N], float [R2N]) holding j of the newest plane, u of the two
-// before it.
+// Rings (offsets in floats): rho float2 [3][R2N]; C [3] x float2 [3][R2N]
+// ((xx, xy), (yy, yz), (xz, zz)); uj [3] x (float2 [R2N], float [R2N])
+// holding j of the newest plane, u of the two before it.
 template <int TY>
 struct RingDB {
     static constexpr int R2N = Geom<TY>::R2N;
     static_assert(R2N % 4 == 0, "ring alignment");
-    static constexpr int RHO = 0, PI = 6 * R2N, C = PI + 6 * R2N, UJ = C + 18 * R2N;
+    static constexpr int RHO = 0, C = 6 * R2N, UJ = C + 18 * R2N;
     static constexpr int FLOATS = UJ + 9 * R2N;
     __device__ static float2 *rho(int s) { return reinterpret_cast<float2 *>(smem() + RHO) + s * R2N; }
-    __device__ static float2 *pi(int s) { return reinterpret_cast<float2 *>(smem() + PI) + s * R2N; }
     __device__ static float2 *c(int s, int k) { return reinterpret_cast<float2 *>(smem() + C + (s * 3 + k) * 2 * R2N); }
     __device__ static float2 *uxy(int s) { return reinterpret_cast<float2 *>(smem() + UJ + s * 3 * R2N); }
     __device__ static float *uz(int s) { return smem() + UJ + s * 3 * R2N + 2 * R2N; }
 };
 
-// Staging: NB population buffers (box BW x (TY+4) x 38 from XPAD cells left
-// of the tile; reduced forms: then the offset densities, 36 x (TY+4) float2
-// from 2 cells left) and one conformation buffer (40 x (TY+4) x 6 from 4
-// cells left).
+// Staging: NB buffers, each a whole plane: the populations (box
+// BW x (TY+4) x 38 from XPAD cells left of the tile), the conformation (box
+// 40 x (TY+4) x 6 from 4 cells left) and, in the reduced forms, the offset
+// densities (36 x (TY+4) float2 from 2 cells left); one barrier each.
 template <typename T, int TY>
 struct StageDB {
-    static constexpr int NB = sizeof(T) == 4 ? 2 : 3;
+    static constexpr int NB = 2;
     static constexpr int XPAD = 16 / (int)sizeof(T);
     static constexpr int BW = 32 + 2 * XPAD, BH = TY + 4;
     static constexpr int POP_PLANE = BW * BH;
     static constexpr u32 POP_BYTES = (u32)(POP_PLANE * 2 * Q * sizeof(T));
+    static constexpr int C_PLANE = 40 * BH;
+    static constexpr u32 C_OFF = (POP_BYTES + 127u) & ~127u;
+    static constexpr u32 C_BYTES = (u32)(C_PLANE * 6 * sizeof(float));
     static constexpr bool DENS = sizeof(T) == 2;
-    static constexpr u32 D_OFF = (POP_BYTES + 127u) & ~127u;
+    static constexpr u32 D_OFF = (C_OFF + C_BYTES + 127u) & ~127u;
     static constexpr u32 D_BYTES = DENS ? (u32)(36 * BH * sizeof(float2)) : 0u;
     static constexpr u32 PBUF = (D_OFF + D_BYTES + 127u) & ~127u;
-    static constexpr int C_PLANE = 40 * BH;
-    static constexpr u32 C_BYTES = (u32)(C_PLANE * 6 * sizeof(float));
-    static constexpr u32 CBUF = (C_BYTES + 127u) & ~127u;
 };
 
 template <typename T>
 constexpr size_t db_smem_bytes() {
-    return sizeof(float) * RingDB<DTY>::FLOATS + 128 + StageDB<T, DTY>::NB * StageDB<T, DTY>::PBUF +
-           StageDB<T, DTY>::CBUF;
+    return sizeof(float) * RingDB<DTY>::FLOATS + 128 + StageDB<T, DTY>::NB * StageDB<T, DTY>::PBUF;
 }
 static_assert(db_smem_bytes<float>() <= 227 * 1024 - 512, "FP32 staging does not fit");
 static_assert(db_smem_bytes<__half>() <= 227 * 1024 - 512, "FP16 staging does not fit");
@@ -90,8 +92,8 @@ __device__ __forceinline__ void tm_wait_ld9(u32 *r) {
 }
 
 template <typename T>
-__device__ __forceinline__ void m_load_region_db(const StepInst &I, const T *sp, const float *sc, int gx, int gy,
-                                                 u32 n, MCell &m) {
+__device__ __forceinline__ void m_load_region_db(const StepInst &I, const T *sp, int gx, int gy, u32 n, MCell &m) {
+    const float *sc = reinterpret_cast<const float *>(reinterpret_cast<const char *>(sp) + StageDB<T, DTY>::C_OFF);
     using St = StageDB<T, DTY>;
     float2 o = make_float2(0.f, 0.f);
     if (Store<T>::offset) {
@@ -133,12 +135,15 @@ __device__ __forceinline__ void m_store_db(const StepInst &I, const MCell &m, in
     Rg::c(s, 0)[idx] = make_float2(m.c[0], m.c[3]);
     Rg::c(s, 1)[idx] = make_float2(m.c[1], m.c[5]);
     Rg::c(s, 2)[idx] = make_float2(m.c[4], m.c[2]);
-    float a = 0.f, fp = 1.f;
-    if (I.visc_comp >= 0) {
-        a = I.pi_coef * (I.visc_comp == 0 ? r.x : r.y) / (r.x + r.y);
-        fp = peterlin(I.L2, m.c[0], m.c[1], m.c[2]);
-    }
-    Rg::pi(s)[idx] = make_float2(a * fp, a);
+}
+
+// Stress scalars (a f, a) of Pi = a (f C) - a I at a cell with densities
+// rho2 and conformation diagonal (cxx, cyy, czz): a = (eta_P/tau_P) chi,
+// chi = rho_visc / rho, f the Peterlin factor of Eq. 2.
+__device__ __forceinline__ float2 stress_scalars(const StepInst &I, float2 rho2, float cxx, float cyy, float czz) {
+    const float a = I.pi_coef * (I.visc_comp == 0 ? rho2.x : rho2.y) / (rho2.x + rho2.y);
+    const float fp = peterlin(I.L2, cxx, cyy, czz);
+    return make_float2(a * fp, a);
 }
 
 // Stage F for one cell of plane q (ring slots s3 of planes q-1, q, q+1):
@@ -164,16 +169,24 @@ __device__ __forceinline__ void stage_f_cell_db(const StepInst &I, int idx, cons
     }
     float FP[3] = {0.f, 0.f, 0.f};
     if (I.visc_comp >= 0) {
-        const float2 *pc = Rg::pi(s3[1]);
-        const float2 Ax = pc[idx + 1], Bx = pc[idx - 1], Ay = pc[idx + RX], By = pc[idx - RX];
-        const float2 Az = Rg::pi(s3[2])[idx], Bz = Rg::pi(s3[0])[idx];
         const float2 *c0 = Rg::c(s3[1], 0), *c1 = Rg::c(s3[1], 1), *c2 = Rg::c(s3[1], 2);
-        const float2 xp0 = c0[idx + 1], xm0 = c0[idx - 1];
-        const float xp2 = c2[idx + 1].x, xm2 = c2[idx - 1].x;
-        const float yp0 = c0[idx + RX].y, ym0 = c0[idx - RX].y;
+        // the face neighbours' conformation: pairs (xx, xy), (yy, yz), (xz, zz)
+        const float2 xp0 = c0[idx + 1], xm0 = c0[idx - 1], xp1 = c1[idx + 1], xm1 = c1[idx - 1];
+        const float2 xp2v = c2[idx + 1], xm2v = c2[idx - 1];
+        const float2 yp0v = c0[idx + RX], ym0v = c0[idx - RX], yp2v = c2[idx + RX], ym2v = c2[idx - RX];
         const float2 yp1 = c1[idx + RX], ym1 = c1[idx - RX];
+        const float2 zp0v = Rg::c(s3[2], 0)[idx], zm0v = Rg::c(s3[0], 0)[idx];
+        const float2 zp1v = Rg::c(s3[2], 1)[idx], zm1v = Rg::c(s3[0], 1)[idx];
         const float2 zp2 = Rg::c(s3[2], 2)[idx], zm2 = Rg::c(s3[0], 2)[idx];
-        const float zp1 = Rg::c(s3[2], 1)[idx].y, zm1 = Rg::c(s3[0], 1)[idx].y;
+        const float2 Ax = stress_scalars(I, rc[idx + 1], xp0.x, xp1.x, xp2v.y);
+        const float2 Bx = stress_scalars(I, rc[idx - 1], xm0.x, xm1.x, xm2v.y);
+        const float2 Ay = stress_scalars(I, rc[idx + RX], yp0v.x, yp1.x, yp2v.y);
+        const float2 By = stress_scalars(I, rc[idx - RX], ym0v.x, ym1.x, ym2v.y);
+        const float2 Az = stress_scalars(I, rp[idx], zp0v.x, zp1v.x, zp2.y);
+        const float2 Bz = stress_scalars(I, rm[idx], zm0v.x, zm1v.x, zm2.y);
+        const float xp2 = xp2v.x, xm2 = xm2v.x;
+        const float yp0 = yp0v.y, ym0 = ym0v.y;
+        const float zp1 = zp1v.y, zm1 = zm1v.y;
         float gxd = Ax.x * xp0.x - Bx.x * xm0.x;
         float gyd = Ay.x * yp0 - By.x * ym0;
         float gzd = Az.x * zp2.x - Bz.x * zm2.x;
@@ -271,23 +284,19 @@ __device__ __forceinline__ bool stage_u_cell_db(const StepInst &I, int idx, int 
     return c[0] + c[1] + c[2] < I.L2;
 }
 
+// One thread: copy plane `plane` (clamped to the lattice) of item P into the
+// staging buffer at dst, completing on bar.
 template <typename T>
-__device__ __forceinline__ void issue_pop_db(const StepArgs &A, const ItemPos &P, int plane, u32 dst, u32 bar,
-                                             u32 go) {
+__device__ __forceinline__ void issue_stage_db(const StepArgs &A, const ItemPos &P, int plane, u32 dst, u32 bar,
+                                               u32 go) {
     using St = StageDB<T, DTY>;
     const StepInst &I = A.inst[P.k];
     const int z = min(max(plane, 0), I.Lz - 1);
     const bool dcopy = St::DENS && I.dens_in != nullptr;
-    mbar_expect_p(bar, St::POP_BYTES + (dcopy ? St::D_BYTES : 0u), go);
+    mbar_expect_p(bar, St::POP_BYTES + St::C_BYTES + (dcopy ? St::D_BYTES : 0u), go);
     tma_box4_p(&I.maps->pop, dst, bar, P.bx * 32 - St::XPAD, P.by * DTY - 2, z, go);
+    tma_box4_p(&I.maps->c, dst + St::C_OFF, bar, P.bx * 32 - 4, P.by * DTY - 2, z, go);
     if (dcopy) tma_box3_p(&I.maps->dens, dst + St::D_OFF, bar, P.bx * 32 - 2, P.by * DTY - 2, z, go);
-}
-
-__device__ __forceinline__ void issue_c_db(const StepArgs &A, const ItemPos &P, int plane, u32 dst, u32 bar, u32 go) {
-    const StepInst &I = A.inst[P.k];
-    const int z = min(max(plane, 0), I.Lz - 1);
-    mbar_expect_p(bar, StageDB<float, DTY>::C_BYTES, go);
-    tma_box4_p(&I.maps->c, dst, bar, P.bx * 32 - 4, P.by * DTY - 2, z, go);
 }
 
 template <typename T>
@@ -303,63 +312,43 @@ k_fused_db(const __grid_constant__ StepArgs A) {
     __shared__ u32 s_rows[RY];
     __shared__ u32 s_cols[RX];
     __shared__ u32 s_tmem;
-    __shared__ __align__(8) unsigned long long s_pbar[NB];   // population buffers filled
-    __shared__ __align__(8) unsigned long long s_cbar;       // conformation buffer filled
-    // every thread has read what it needs from the staging buffers (NT arrivals per plane)
-    __shared__ __align__(8) unsigned long long s_empty;
+    __shared__ __align__(8) unsigned long long s_bar[NB];   // staging buffer b filled
     __shared__ int s_item[2];
 
     const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
     const int idx_in = (ty + 2) * RX + (tx + 2);
     const u32 smem_base = smem_addr(lbfe_smem4);
-    const u32 pbuf0 = (smem_base + (u32)(sizeof(float) * Rg::FLOATS) + 127u) & ~127u;
-    const u32 cbuf = pbuf0 + (u32)NB * St::PBUF;
+    const u32 buf0 = (smem_base + (u32)(sizeof(float) * Rg::FLOATS) + 127u) & ~127u;
     const char *gen0 = reinterpret_cast<const char *>(lbfe_smem4) - smem_base;   // generic = gen0 + shared address
-    const float *stage_c = reinterpret_cast<const float *>(gen0 + cbuf);
-    const u32 cbar = smem_addr(&s_cbar), ebar = smem_addr(&s_empty);
-    // The copies are issued by lane 0 of the last warp, which has no halo
-    // cells in stage M: as soon as every thread has read its cells from the
-    // staging buffers it starts the next copies (an issue can stall while
-    // the SM's copy engine is busy with the copy in flight; that thread has
-    // the slack to absorb it), before the stage-M barrier.
-    constexpr int kIssuer = NT - 32;
-    static_assert(kIssuer >= Gm::NRING2 && kIssuer >= Gm::NRING1, "the issuing warp has no halo cells");
-    u32 eparity = 0;     // issuer: phase parity of the next buffers-read phase
-    // phase parities of the next completion waited for, per barrier
-    u32 ppar = 0;        // bit b: population buffer b
-    u32 cpar = 0;
-    // issuing thread: bit b of pany = a copy went out on population
-    // barrier b, of pcnt = the parity of their count (the last one's phase
-    // parity is its complement); likewise for the conformation barrier
-    u32 pany = 0, pcnt = 0, cany = 0, ccnt = 0;
+    u32 par = 0;         // bit b: phase parity of the next completion of buffer b
+    // issuing thread (thread 0): bit b of bany = a copy went out on buffer b,
+    // of bcnt = the parity of their count (the last one's phase parity is
+    // its complement)
+    u32 bany = 0, bcnt = 0;
     bool expired = false;
 
     if (ty == 0) tm_alloc(&s_tmem, kDbTmemCols);
     if (t == 0) {
 #pragma unroll
-        for (int b = 0; b < NB; ++b) mbar_init(smem_addr(&s_pbar[b]));
-        mbar_init(cbar);
-        mbar_init_count(ebar, NT);
+        for (int b = 0; b < NB; ++b) mbar_init(smem_addr(&s_bar[b]));
     }
     tm_fence_before();
     __syncthreads();
     tm_fence_after();
     const u32 tm_warp = s_tmem + ((u32)(32 * (ty & 3)) << 16) + (u32)((ty >> 2) * 256);
 
-    // Block b starts with item b; further items from the launch's counter,
-    // one ahead.  Plane loads are numbered per block across its items; load
-    // k uses population buffer k % NB.
-    if (t == 0) s_item[0] = blockIdx.x;
-    if (t == kIssuer) {
+    // Block b starts with item b; further items come from the launch's
+    // counter, one ahead.  Plane loads are numbered per block across its
+    // items; load k goes to buffer k % NB.
+    if (t == 0) {
+        s_item[0] = blockIdx.x;
         if ((int)blockIdx.x < A.total_items) {
             const ItemPos P0 = item_pos<TY>(A, blockIdx.x);
             if (A.inst[P0.k].tma) {
 #pragma unroll
                 for (int b = 0; b < NB; ++b)
-                    issue_pop_db<T>(A, P0, P0.z0 - 2 + b, pbuf0 + (u32)b * St::PBUF, smem_addr(&s_pbar[b]), 1u);
-                pany = pcnt = (1u << NB) - 1u;
-                issue_c_db(A, P0, P0.z0 - 2, cbuf, cbar, 1u);
-                cany = ccnt = 1u;
+                    issue_stage_db<T>(A, P0, P0.z0 - 2 + b, buf0 + (u32)b * St::PBUF, smem_addr(&s_bar[b]), 1u);
+                bany = bcnt = (1u << NB) - 1u;
             }
         }
     }
@@ -410,7 +399,7 @@ k_fused_db(const __grid_constant__ StepArgs A) {
             const int q = p - 1, r = p - 2;
             const int s3[3] = {ring3(q - 1), ring3(q), ring3(q + 1)};   // planes r, q, p
             const u32 pb = kload % (u32)NB;
-            const T *stage = reinterpret_cast<const T *>(gen0 + pbuf0 + pb * St::PBUF);
+            const T *stage = reinterpret_cast<const T *>(gen0 + buf0 + pb * St::PBUF);
             // ---------------- stage M(p)
             {
                 const u32 pl = (u32)(min(max(p, 0), Lz - 1) * LxLy);
@@ -418,21 +407,15 @@ k_fused_db(const __grid_constant__ StepArgs A) {
                 // halo cells across a periodic seam (outside the copied box)
                 if (h_on && !(tma && h_dom)) m_load<T>(I, fin, Cin, S, pl + h_ofs, mh);
                 if (tma) {
-                    if (!expired && !mbar_wait(smem_addr(&s_pbar[pb]), (ppar >> pb) & 1u)) expired = true;
-                    ppar ^= 1u << pb;
-                    if (!expired && !mbar_wait(cbar, cpar)) expired = true;
-                    cpar ^= 1u;
+                    if (!expired && !mbar_wait(smem_addr(&s_bar[pb]), (par >> pb) & 1u)) expired = true;
+                    par ^= 1u << pb;
                 }
-                // the staged halo cell first, then the own cell: every thread is
-                // then done with the staging buffers
-                if (h_on && tma && h_dom) m_load_region_db<T>(I, stage, stage_c, h_gx, h_gy, pl + h_ofs, mh);
                 {
                     MCell m;
                     if (tma && valid)
-                        m_load_region_db<T>(I, stage, stage_c, tx + 2, ty + 2, pl + ofs_in, m);
+                        m_load_region_db<T>(I, stage, tx + 2, ty + 2, pl + ofs_in, m);
                     else
                         m_load<T>(I, fin, Cin, S, pl + ofs_in, m);
-                    mbar_arrive(ebar);
                     m_store_db(I, m, idx_in, s3[2]);
                     tm_store38(tm_warp + (u32)((p & 1) * 64), reinterpret_cast<const float *>(m.ab));
                     // own C of plane p, for stage U(p + 1)
@@ -440,45 +423,34 @@ k_fused_db(const __grid_constant__ StepArgs A) {
                     tm_st4(tc, m.c);
                     tm_st2(tc + 4, m.c + 4);
                 }
-                if (h_on) m_store_db(I, mh, h_idx, s3[2]);
-            }
-            if (t == kIssuer) {
-                if (!expired && !mbar_wait(ebar, eparity)) expired = true;
-                eparity ^= 1u;
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                const u32 go = expired ? 0u : 1u;
-                // population load kload + NB into the buffer just read; the
-                // conformation of load kload + 1
-                auto ahead = [&](int d, ItemPos &Po, int &plane) -> bool {
-                    if (p + d <= z1 + 1) {
-                        Po = P;
-                        plane = p + d;
-                        return true;
-                    }
-                    // published at the item's first plane (at least three planes ago)
-                    const int nx = s_item[slot ^ 1];
-                    if (nx >= A.total_items) return false;
-                    Po = item_pos<TY>(A, nx);
-                    plane = Po.z0 - 2 + (p + d - (z1 + 2));
-                    return true;
-                };
-                // the conformation first: the next stage M needs it, and the
-                // copies queued on an SM complete in the order issued
-                ItemPos Po;
-                int plane;
-                if (ahead(1, Po, plane) && A.inst[Po.k].tma) {
-                    issue_c_db(A, Po, plane, cbuf, cbar, go);
-                    cany |= go;
-                    ccnt ^= go;
-                }
-                if (ahead(NB, Po, plane) && A.inst[Po.k].tma) {
-                    issue_pop_db<T>(A, Po, plane, pbuf0 + pb * St::PBUF, smem_addr(&s_pbar[pb]), go);
-                    pany |= go << pb;
-                    pcnt ^= go << pb;
+                if (h_on) {
+                    if (tma && h_dom) m_load_region_db<T>(I, stage, h_gx, h_gy, pl + h_ofs, mh);
+                    m_store_db(I, mh, h_idx, s3[2]);
                 }
             }
             __syncthreads();
-            if (t == 0 && p == z0 - 2) s_item[slot ^ 1] = next_t0;
+            if (t == 0) {
+                if (p == z0 - 2) s_item[slot ^ 1] = next_t0;
+                // the buffer just read takes the plane NB loads ahead (of this
+                // item, else of the next one, whose id this thread took)
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                const u32 go = expired ? 0u : 1u;
+                ItemPos Po = P;
+                int plane = p + NB;
+                bool have = true;
+                if (plane > z1 + 1) {
+                    have = next_t0 < A.total_items;
+                    if (have) {
+                        Po = item_pos<TY>(A, next_t0);
+                        plane = Po.z0 - 2 + (p + NB - (z1 + 2));
+                    }
+                }
+                if (have && A.inst[Po.k].tma) {
+                    issue_stage_db<T>(A, Po, plane, buf0 + pb * St::PBUF, smem_addr(&s_bar[pb]), go);
+                    bany |= go << pb;
+                    bcnt ^= go << pb;
+                }
+            }
             // the collision's populations and stage U's own-cell values of
             // plane r - 1 start to come back from TMEM here, ahead of stage F
             const bool doX = q >= z0 && q < z1, doU = r >= z0 && r < z1;
@@ -566,14 +538,13 @@ k_fused_db(const __grid_constant__ StepArgs A) {
     }
 
     if (t == 0 && A.total_items > (int)gridDim.x) release_work_counters(A.work);
-    if (expired && t == kIssuer) {
+    if (expired && t == 0) {
         // copies issued but not waited for may still be in flight: wait,
         // bounded, for the last phase of each barrier before the block's
         // shared memory is released
 #pragma unroll
         for (int b = 0; b < NB; ++b)
-            if ((pany >> b) & 1u) mbar_wait(smem_addr(&s_pbar[b]), ((pcnt >> b) & 1u) ^ 1u);
-        if (cany) mbar_wait(cbar, ccnt ^ 1u);
+            if ((bany >> b) & 1u) mbar_wait(smem_addr(&s_bar[b]), ((bcnt >> b) & 1u) ^ 1u);
     }
     if (expired) atomicOr(A.status, kFlagTimeout);
     tm_wait_st();
