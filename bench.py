@@ -456,7 +456,7 @@ def autotune_summary(shape):
         return None
     best = {}
     for kern, ty, _zc, ms in shape.get("trials", []):
-        key = f"{['cell', 'pair', 'pipelined'][kern]}_32x{ty}"
+        key = f"{'pair' if kern else 'cell'}_32x{ty}"
         best[key] = round(min(ms, best.get(key, ms)), 5)
     return {"best_ms_per_step": best}
 

@@ -201,14 +201,11 @@ lbfe_status lbfe_set_field(lbfe_handle *h, int k, int which, const void *host_sr
  * its parameter space). */
 int lbfe_launches_per_step(const lbfe_handle *h);
 
-/* Variants of the time-step kernel.  All compute the same step (results
+/* Variants of the time-step kernel.  Both compute the same step (results
  * agree to FP32 rounding); they differ in speed only. */
 typedef enum {
     LBFE_STEP_CELL = 0,   /* one cell per thread, tiles of 32 x tile_y cells, tile_y in {8, 12, 16} */
-    LBFE_STEP_PAIR = 1,   /* two x-adjacent cells per thread, 32 x 16 tiles; needs even Lx everywhere */
-    LBFE_STEP_CELL_PIPELINED = 2  /* one cell per thread, 32 x 8 tiles, with the copies of the next
-                                     planes in flight two (FP32) or three (FP16 / BF16) planes ahead;
-                                     first-order advection only */
+    LBFE_STEP_PAIR = 1    /* two x-adjacent cells per thread, 32 x 16 tiles; needs even Lx everywhere */
 } lbfe_step_kernel;
 
 /* Launch shape of the step kernel: variant (lbfe_step_kernel), column-tile
@@ -217,8 +214,7 @@ typedef enum {
  * A new handle starts with LBFE_STEP_CELL, tile_y 8 (FP32, or any precision
  * with LBFE_ADVECTION_UPWIND2_MINMOD) or 12 (FP16 / BF16 storage) and the
  * automatic z-chunk.  With LBFE_ADVECTION_UPWIND2_MINMOD only
- * LBFE_STEP_CELL at tile_y 8 is accepted; LBFE_STEP_CELL_PIPELINED takes
- * tile_y 8 only.
+ * LBFE_STEP_CELL at tile_y 8 is accepted.
  * LBFE_ERR_BAD_PARAM for an unsupported combination.  Synchronises the
  * stream. */
 lbfe_status lbfe_tune(lbfe_handle *h, int step_kernel, int tile_y, int z_chunk);

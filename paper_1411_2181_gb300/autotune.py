@@ -1,9 +1,8 @@
 """Autotuner of the step kernel's launch shape.
 
-The step kernel runs one block per column tile and z-chunk, in one of three
-variants: one cell per thread with tiles of 32 x TY cells (TY = 8, 12 or 16),
-two x-adjacent cells per thread with 32 x 16 tiles (even Lx only), or one
-cell per thread on 32 x 8 tiles with the plane copies pipelined.  The
+The step kernel runs one block per column tile and z-chunk, in one of two
+variants: one cell per thread with tiles of 32 x TY cells (TY = 8, 12 or 16)
+or two x-adjacent cells per thread with 32 x 16 tiles (even Lx only).  The
 variant, tile height and chunk depth change speed only (the fields agree to
 FP32 rounding).  ``tune`` times each candidate on a scratch solver built
 from the same parameters, keeps the fastest, and caches the choice in a JSON
@@ -26,7 +25,7 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "auto
 
 def _key(params: list[Params], gpu: str) -> str:
     dims = ";".join(f"{p.Lx}x{p.Ly}x{p.Lz}" for p in params)
-    return f"{gpu}|v3|prec{params[0].precision}|adv{params[0].advection}|n{len(params)}|{dims}"
+    return f"{gpu}|v2|prec{params[0].precision}|adv{params[0].advection}|n{len(params)}|{dims}"
 
 
 def _load(path):
@@ -45,7 +44,7 @@ def candidates(params: list[Params]):
     if params[0].advection:
         shapes = [(0, 8)]        # the second-order advection runs at 8-row tiles only
     else:
-        shapes = [(0, ty) for ty in TILE_Y] + [(2, 8)]
+        shapes = [(0, ty) for ty in TILE_Y]
         if all(p.Lx % 2 == 0 for p in params):
             shapes.append((1, 16))
     return [(k, ty, zc) for k, ty in shapes for zc in Z_CHUNKS if zc <= lz]

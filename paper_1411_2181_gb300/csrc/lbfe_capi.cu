@@ -200,8 +200,6 @@ static lbfe_status configure_fused(lbfe_handle *h, int step_kernel, int tile_y, 
         if (tile_y != 16) return LBFE_ERR_BAD_PARAM;
         for (auto &I : h->inst)
             if (I.Lx % 2) return LBFE_ERR_BAD_PARAM;
-    } else if (step_kernel == LBFE_STEP_CELL_PIPELINED) {
-        if (tile_y != 8) return LBFE_ERR_BAD_PARAM;
     } else if (step_kernel != LBFE_STEP_CELL || (tile_y != 8 && tile_y != 12 && tile_y != 16)) {
         return LBFE_ERR_BAD_PARAM;
     }

@@ -464,7 +464,6 @@ cudaError_t fused_group(const LaunchCtx &c, int cur, int k0, int k1) {
     if (a.total_items <= 0) return cudaSuccess;
     const int grid = a.total_items < c.fused_slots ? a.total_items : c.fused_slots;
     if (c.step_kernel == LBFE_STEP_PAIR) return step_pair_launch(a, grid, c.precision, c.stream);
-    if (c.step_kernel == LBFE_STEP_CELL_PIPELINED) return step_db_launch(a, grid, c.precision, c.stream);
     return step_cell_launch(a, grid, c.tile_y, c.precision, c.advection, c.stream);
 }
 
@@ -553,7 +552,6 @@ cudaError_t fused_pop_maps(const InstDev &I, int precision, int tile_y, bool sho
 
 cudaError_t fused_prepare(int step_kernel, int tile_y, int precision, int advection, int *blocks_per_sm) {
     if (step_kernel == LBFE_STEP_PAIR) return step_pair_prepare(precision, blocks_per_sm);
-    if (step_kernel == LBFE_STEP_CELL_PIPELINED) return step_db_prepare(precision, blocks_per_sm);
     return step_cell_prepare(tile_y, precision, advection, blocks_per_sm);
 }
 

@@ -106,8 +106,6 @@ cudaError_t step_cell_launch(const StepArgs &a, int grid, int tile_y, int precis
 cudaError_t step_cell_prepare(int tile_y, int precision, int advection, int *blocks_per_sm);
 cudaError_t step_pair_launch(const StepArgs &a, int grid, int precision, cudaStream_t st);
 cudaError_t step_pair_prepare(int precision, int *blocks_per_sm);
-cudaError_t step_db_launch(const StepArgs &a, int grid, int precision, cudaStream_t st);
-cudaError_t step_db_prepare(int precision, int *blocks_per_sm);
 
 namespace {
 

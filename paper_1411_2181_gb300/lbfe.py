@@ -25,7 +25,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ct.CDLL(LIB_PATH)
 
 FIELD_F, FIELD_C, FIELD_RHO, FIELD_U = 0, 1, 2, 3
-STEP_CELL, STEP_PAIR, STEP_CELL_PIPELINED = 0, 1, 2   # lbfe_step_kernel
+STEP_CELL, STEP_PAIR = 0, 1   # lbfe_step_kernel
 INJECT_SHORT_COPIES = 1       # lbfe_test_inject
 
 OK, ERR_BAD_PARAM, ERR_NO_MEMORY, ERR_CUDA, ERR_DIVERGED, ERR_TIMEOUT, ERR_STATE, ERR_IO = range(8)

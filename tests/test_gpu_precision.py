@@ -62,12 +62,11 @@ def test_reduced_storage_errors(runs, prec, tol_D, tol_theta, tol_mass):
 def test_reduced_storage_launch_shapes_agree(L, prec):
     """The reduced storage forms give the same fields, to a few storage ulps,
     at every launch shape: 8- and 12-row tiles (copies of the radius-2
-    region), 16-row tiles (own-cell copies), two cells per thread and the
-    pipelined 8-row kernel."""
+    region), 16-row tiles (own-cell copies) and two cells per thread."""
     p0, rho, _ = configs.config3(crop=True)
     p = replace(p0, precision=prec)
     out = []
-    for kernel, ty in ((0, 8), (0, 12), (0, 16), (1, 16), (2, 8)):
+    for kernel, ty in ((0, 8), (0, 12), (0, 16), (1, 16)):
         s = L.Solver(p)
         s.tune(ty, 0, kernel)
         s.init(0, rho)

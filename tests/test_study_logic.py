@@ -96,15 +96,15 @@ def test_range_ends_need_one_run_when_predicted(fake_runs):
 
 def test_autotune_candidates():
     """Launch shapes the autotuner tries: every tile height of the one-cell
-    kernel, its pipelined 8-row form, the two-cell kernel only when every Lx
-    is even, and only the plain 8-row kernel with the second-order advection
-    scheme; z-chunks no deeper than the deepest instance."""
+    kernel, the two-cell kernel only when every Lx is even, and only 8-row
+    tiles with the second-order advection scheme; z-chunks no deeper than
+    the deepest instance."""
     from dataclasses import replace
     from paper_1411_2181_gb300 import autotune
     from paper_1411_2181_gb300.params import Params
     p = Params(Lx=64, Ly=32, Lz=24)
     shapes = {(k, ty) for k, ty, _ in autotune.candidates([p])}
-    assert shapes == {(0, 8), (0, 12), (0, 16), (1, 16), (2, 8)}
+    assert shapes == {(0, 8), (0, 12), (0, 16), (1, 16)}
     assert all(zc <= 24 for _, _, zc in autotune.candidates([p]))
     odd = {(k, ty) for k, ty, _ in autotune.candidates([p, replace(p, Lx=63)])}
     assert (1, 16) not in odd
