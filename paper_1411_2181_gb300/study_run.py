@@ -1,132 +1,225 @@
-"""Train the proposal network on solver runs and compare Ca_cr searches.
+"""Collect solver runs, train the proposal network, compare Ca_cr searches.
 
-python -m paper_1411_2181_gb300.study_run --train 1024 --triples 16 --out report.json
+The three steps can run in separate processes (the collection is the
+expensive one: a full simulation per case):
 
-1. ``--train`` cases drawn over (Ca, De, lambda, 2R/W, phase) are simulated
-   in batches; their verdicts and shapes are the training set.
-2. The network is trained by the CUDA kernels (AdamW, BF16 weights).
-3. For ``--triples`` held-out (De, lambda, 2R/W, phase) triples (seed 5), Ca_cr
-   is searched by plain bisection and with the network's bracket; both give
-   brackets of width <= 0.02 confirmed by full runs.  The report lists, per
-   mode, the number of full simulations, batched rounds and wall time, and
-   per triple both brackets.
+  python -m paper_1411_2181_gb300.study_run collect --n 512 --seed 100 --out runs_100.jsonl
+  python -m paper_1411_2181_gb300.study_run train --data runs_100.jsonl,runs_101.jsonl --params-out net.npy
+  python -m paper_1411_2181_gb300.study_run search --params net.npy --triples 16 --out report.json
+  python -m paper_1411_2181_gb300.study_run trend --out trend.json
+
+collect  simulates cases drawn by study.sample_cases (batched full runs) and
+         appends one JSON line per run: the case and its verdict (break-up,
+         steady D and theta, necks, break-up time, blown up or not);
+train    fits the network to the collected runs with the CUDA kernels
+         (AdamW, BF16 weights, FP32 accumulation), holding out one run in
+         eight to report its accuracy, and saves the FP32 parameters;
+search   searches Ca_cr for held-out (De, lambda, 2R/W) triples of the
+         matrix-viscoelastic family (seed 5), by plain bisection and with the
+         network's bracket; both end with brackets of width <= 0.02 whose
+         ends are full-run verdicts.  The report lists, per mode, the full
+         simulations, batched rounds and wall time, and per triple both
+         brackets;
+trend    Ca_cr by bisection against the confinement for Newtonian, droplet-
+         and matrix-viscoelastic droplets (the trends of Figs. 2 and 4).
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import time
 
 import numpy as np
 
-from . import mlp, study
+from . import study
+
+HELD_OUT_DE = (1.0, 1.5, 2.0)
 
 
 def held_out_triples(n: int, seed: int = 5):
+    """(De, lambda, 2R/W, phase) of the matrix-viscoelastic family, whose
+    Ca_cr lies inside the search range at the study's resolution; the
+    confinements are continuous draws, so no triple equals a training
+    case's."""
     rng = np.random.default_rng(seed)
-    return [(float(rng.choice([0.0, 0.5, 1.0, 2.0])), float(rng.choice(study.LAMBDAS)),
-             float(rng.uniform(study.CONF_MIN + 0.02, study.CONF_MAX - 0.02)), int(rng.choice([1, 2])))
-            for _ in range(n)]
+    out = []
+    while len(out) < n:
+        t = (float(rng.choice(HELD_OUT_DE)), float(rng.choice(study.LAMBDAS)),
+             float(round(rng.uniform(study.CONF_MIN + 0.02, study.CONF_MAX - 0.02), 4)), 2)
+        if t not in out:
+            out.append(t)
+    return out
 
 
-def CA_IN(s) -> bool:
+def interior(s) -> bool:
     """Ca_cr strictly inside the search range (not at either end)."""
     return study.CA_MIN < 0.5 * (s.lo + s.hi) < study.CA_MAX
 
 
-def main(argv=None):
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--train", type=int, default=1024)
-    ap.add_argument("--triples", type=int, default=16)
-    ap.add_argument("--epochs", type=int, default=1500)
-    ap.add_argument("--delta", type=float, default=0.06)
-    ap.add_argument("--out", default=None)
-    ap.add_argument("--params-out", default=None)
-    ap.add_argument("--params-in", default=None, help="reuse a trained network (skips the training runs)")
-    ap.add_argument("--trend", action="store_true",
-                    help="only Ca_cr by bisection against the confinement 2R/W for Newtonian, DV and MV "
-                         "droplets at De = 2, lambda = 1 (the trends of Figs. 2 and 4, reduced domains)")
-    ap.add_argument("--trend-lambda", type=float, default=1.0, help="viscosity ratio of the --trend cases")
-    a = ap.parse_args(argv)
-    if a.trend:
-        return trend(a.out, a.trend_lambda)
+def _case_json(c, v):
+    return {"Ca": c.Ca, "De": c.De, "lam": c.lam, "conf": c.conf, "L2": c.L2, "phase": c.phase, "seed": c.seed,
+            "broken": bool(v.broken), "D": float(v.D), "theta": float(v.theta), "necks": int(v.necks),
+            "t_break": None if v.t_break != v.t_break else float(v.t_break), "ok": bool(v.ok)}
 
-    report = {}
+
+def collect(n: int, seed: int, out: str, batch: int = 64):
+    """Simulate n training cases; one JSON line per run (written per batch)."""
+    stats = {}
     t0 = time.perf_counter()
-    net = mlp.MLP(max_batch=max(4096, a.train), bf16=True)
-    if a.params_in:
-        net.set_params(np.load(a.params_in))
-        report["network"] = {"loaded": a.params_in}
-    else:
-        st_train = {}
-        cases, verdicts = study.training_set(a.train, seed=100, stats=st_train)
-        report["training_runs"] = dict(st_train, valid=len(cases), broken=int(sum(v.broken for v in verdicts)))
-        X = study.features(cases)
-        T, M = study.targets(verdicts)
-        # hold out 1/8 of the runs to estimate the network's accuracy
-        n_val = max(1, len(X) // 8)
-        net.set_params(mlp.init_params(0))
-        t1 = time.perf_counter()
-        hist = net.fit(X[n_val:], T[n_val:], M[n_val:], epochs=a.epochs, lr=3e-3, batch=256)
-        train_s = time.perf_counter() - t1
-        yv = net.forward(X[:n_val])
-        acc = float(np.mean((yv[:, 2] > 0) == (T[:n_val, 2] > 0.5)))
-        d_err = float(np.sqrt(np.sum(M[:n_val] * (yv[:, 0] - T[:n_val, 0]) ** 2) / max(1.0, M[:n_val].sum())))
-        report["network"] = {"epochs": a.epochs, "final_loss": hist[-1], "first_loss": hist[0],
-                             "train_seconds": train_s, "val_breakup_accuracy": acc, "val_D_rmse": d_err}
-    if a.params_out:
-        np.save(a.params_out, net.get_params())
+    written = [0]
 
-    triples = held_out_triples(a.triples)
+    def progress(cases, verdicts):
+        with open(out, "a") as fh:
+            for c, v in zip(cases[written[0]:], verdicts[written[0]:]):
+                fh.write(json.dumps(_case_json(c, v)) + "\n")
+        written[0] = len(verdicts)
+
+    open(out, "w").close()
+    study.training_set(n, seed=seed, batch=batch, stats=stats, progress=progress)
+    stats["wall_seconds"] = time.perf_counter() - t0
+    print(json.dumps({"collected": written[0], "seed": seed, "stats": stats}))
+    return stats
+
+
+def load_runs(paths):
+    cases, verdicts = [], []
+    for p in paths:
+        with open(p) as fh:
+            for line in fh:
+                d = json.loads(line)
+                if not d["ok"]:
+                    continue
+                cases.append(study.Case(Ca=d["Ca"], De=d["De"], lam=d["lam"], conf=d["conf"], L2=d["L2"],
+                                        phase=d["phase"], seed=d["seed"]))
+                tb = d["t_break"]
+                verdicts.append(study.Verdict(d["broken"], d["D"], d["theta"], d["necks"],
+                                              float("nan") if tb is None else tb))
+    return cases, verdicts
+
+
+def train(paths, epochs: int = 1500, params_out: str | None = None, seed: int = 0):
+    from . import mlp
+    cases, verdicts = load_runs(paths)
+    X = study.features(cases)
+    T, M = study.targets(verdicts)
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(len(X))
+    X, T, M = X[perm], T[perm], M[perm]
+    n_val = max(1, len(X) // 8)
+    net = mlp.MLP(max_batch=max(4096, len(X)), bf16=True)
+    net.set_params(mlp.init_params(seed))
+    t1 = time.perf_counter()
+    hist = net.fit(X[n_val:], T[n_val:], M[n_val:], epochs=epochs, lr=3e-3, batch=256)
+    train_s = time.perf_counter() - t1
+    yv = net.forward(X[:n_val])
+    acc = float(np.mean((yv[:, 2] > 0) == (T[:n_val, 2] > 0.5)))
+    d_err = float(np.sqrt(np.sum(M[:n_val] * (yv[:, 0] - T[:n_val, 0]) ** 2) / max(1.0, M[:n_val].sum())))
+    info = {"runs": int(len(X)), "broken": int(T[:, 2].sum()), "epochs": epochs, "first_loss": hist[0],
+            "final_loss": hist[-1], "train_seconds": train_s, "val_runs": n_val,
+            "val_breakup_accuracy": acc, "val_D_rmse": d_err}
+    if params_out:
+        np.save(params_out, net.get_params())
+    print(json.dumps(info))
+    return net, info
+
+
+def compare(net, triples, delta: float = 0.06):
+    """Both searches over the same triples; the comparison of the report."""
     sb, stb = study.search_bisect(triples)
-    sm, stm = study.search_mlp(triples, net, delta=a.delta)
+    sm, stm = study.search_mlp(triples, net, delta=delta)
     per = []
     agree = overlap = 0
     for b, m in zip(sb, sm):
         cb, cm = 0.5 * (b.lo + b.hi), 0.5 * (m.lo + m.hi)
         agree += abs(cb - cm) <= 0.01 + 1e-9
         overlap += max(b.lo, m.lo) <= min(b.hi, m.hi) + 1e-12
-        per.append({"triple": b.triple, "bisect": [b.lo, b.hi, b.runs], "mlp": [m.lo, m.hi, m.runs]})
+        per.append({"triple": b.triple, "bisect": [b.lo, b.hi, b.runs], "mlp": [m.lo, m.hi, m.runs],
+                    "interior": bool(interior(b))})
     keys = ("runs", "rounds", "seconds", "lattice_updates", "diverged")
-    report["bisect"] = {k: stb.get(k, 0) for k in keys}
-    report["mlp"] = {k: stm.get(k, 0) for k in keys}
-    report["in_range"] = int(sum(CA_IN(b) for b in sb))
-    report["agree_within_0.01"] = f"{agree}/{len(triples)}"
-    report["brackets_consistent"] = f"{overlap}/{len(triples)}"
-    report["per_triple"] = per
-    report["total_seconds"] = time.perf_counter() - t0
-    txt = json.dumps(report, indent=1)
-    print(txt)
-    if a.out:
-        with open(a.out, "w") as fh:
-            fh.write(txt)
-    return report
+    return {"bisect": {k: stb.get(k, 0) for k in keys}, "mlp": {k: stm.get(k, 0) for k in keys},
+            "interior": int(sum(interior(b) for b in sb)), "triples": len(triples),
+            "agree_within_0.01": int(agree), "brackets_consistent": int(overlap), "delta": delta,
+            "per_triple": per}
 
 
-def trend(out=None, lam=1.0):
+def search(params: str, n_triples: int, out: str | None, delta: float = 0.06, train_info: dict | None = None):
+    from . import mlp
+    net = mlp.MLP(max_batch=4096, bf16=True)
+    net.set_params(np.load(params))
+    t0 = time.perf_counter()
+    rep = compare(net, held_out_triples(n_triples), delta=delta)
+    rep["total_seconds"] = time.perf_counter() - t0
+    rep["regime"] = {"W": study.W, "Lx": study.LX, "Ly": study.LY, "Uw": study.UW, "G": study.G_STUDY,
+                     "Ca_range": [study.CA_MIN, study.CA_MAX], "t_max_tem": study.T_MAX_TEM,
+                     "conf_range": [study.CONF_MIN, study.CONF_MAX]}
+    if train_info:
+        rep["network"] = train_info
+    _emit(rep, out)
+    return rep
+
+
+def trend(out=None, lam=1.0, confs=(0.6, 0.7, 0.8)):
     """Ca_cr (bisection, bracket width 0.02) for Newtonian (De = 0), droplet-
-    and matrix-viscoelastic (De = 2) droplets at viscosity ratio lam and 2R/W in
-    {0.6, 0.7, 0.8} on the study's reduced domains.  Sec. 3 reports, at the
-    paper's sizes, that confinement raises Ca_cr, droplet viscoelasticity
-    raises it further and matrix viscoelasticity lowers it."""
+    and matrix-viscoelastic (De = 2) droplets at viscosity ratio lam against
+    2R/W on the study's domains.  Sec. 3 reports, at the paper's sizes, that
+    droplet viscoelasticity raises Ca_cr and matrix viscoelasticity lowers
+    it, more so under strong confinement."""
     kinds = (("newtonian", 0.0, 1), ("DV", 2.0, 1), ("MV", 2.0, 2))
-    confs = (0.6, 0.7, 0.8)
     triples = [(De, lam, conf, phase) for conf in confs for _, De, phase in kinds]
     t0 = time.perf_counter()
     sb, st = study.search_bisect(triples)
     rows = {}
-    for (name, _, _), i in zip(kinds * len(confs), range(len(triples))):
-        s = sb[i]
-        rows.setdefault(name, []).append({"2R/W": s.triple[2], "Ca_cr": 0.5 * (s.lo + s.hi),
-                                          "bracket": [s.lo, s.hi], "runs": s.runs})
-    report = {"lambda": lam, "trend": rows, "runs": st.get("runs", 0), "rounds": st.get("rounds", 0),
-              "diverged": st.get("diverged", 0), "seconds": time.perf_counter() - t0}
-    txt = json.dumps(report, indent=1)
+    for i, s in enumerate(sb):
+        name = kinds[i % len(kinds)][0]
+        lo_open = s.lo == s.hi == study.CA_MAX
+        rows.setdefault(name, []).append({"2R/W": s.triple[2], "bracket": [s.lo, s.hi],
+                                          "Ca_cr": (None if lo_open else 0.5 * (s.lo + s.hi)),
+                                          "stable_over_range": bool(lo_open), "runs": s.runs})
+    rep = {"lambda": lam, "trend": rows, "runs": st.get("runs", 0), "rounds": st.get("rounds", 0),
+           "diverged": st.get("diverged", 0), "seconds": time.perf_counter() - t0,
+           "Ca_range": [study.CA_MIN, study.CA_MAX]}
+    _emit(rep, out)
+    return rep
+
+
+def _emit(rep, out):
+    txt = json.dumps(rep, indent=1)
     print(txt)
     if out:
         with open(out, "w") as fh:
             fh.write(txt)
-    return report
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    c = sub.add_parser("collect")
+    c.add_argument("--n", type=int, default=512)
+    c.add_argument("--seed", type=int, default=100)
+    c.add_argument("--out", required=True)
+    t = sub.add_parser("train")
+    t.add_argument("--data", required=True, help="comma-separated collect outputs")
+    t.add_argument("--epochs", type=int, default=1500)
+    t.add_argument("--params-out", required=True)
+    s = sub.add_parser("search")
+    s.add_argument("--params", required=True)
+    s.add_argument("--triples", type=int, default=16)
+    s.add_argument("--delta", type=float, default=0.06)
+    s.add_argument("--out", default=None)
+    s.add_argument("--train-info", default=None, help="JSON file of the train step, copied into the report")
+    r = sub.add_parser("trend")
+    r.add_argument("--out", default=None)
+    r.add_argument("--lam", type=float, default=1.0)
+    a = ap.parse_args(argv)
+    if a.cmd == "collect":
+        return collect(a.n, a.seed, a.out)
+    if a.cmd == "train":
+        return train(a.data.split(","), a.epochs, a.params_out)
+    if a.cmd == "search":
+        info = json.load(open(a.train_info)) if a.train_info else None
+        return search(a.params, a.triples, a.out, a.delta, info)
+    return trend(a.out, a.lam)
 
 
 if __name__ == "__main__":

@@ -291,3 +291,37 @@ def test_laplace_law_sphere_3d():
         assert abs(sigma / sigma_cyl - 1) < 0.05, (R, R_eq, dp, sigma, sigma_cyl)
         # a cylinder's law (one curvature) would be off by a factor 2
         assert abs(dp * R_eq / sigma_cyl - 1) > 0.8
+
+
+def test_taylor_small_deformation_in_shear():
+    """Full coupling, small capillary number (Sec. 1 cites Taylor's result):
+    a Newtonian droplet (lambda = 1) in the Couette flow between the moving
+    walls deforms to D = Ca (19 lambda + 16)/(16 lambda + 16) = 35/32 Ca with
+    its major axis near 45 degrees from the flow.  R = 8 in a 48 x 48 x 32
+    box (2R/W = 0.5), Shan-Chen G = 3.8 (the tabulated sigma), Ca = 0.1,
+    wall speed 0.05 (Re = 0.54), started from the Couette profile; after 9
+    emulsion times D is within 15% of 35/32 Ca and theta within 5 degrees of
+    45 (a physics check: the diffuse interface, the confinement and the
+    finite Reynolds number each move the result by several percent)."""
+    G, rin, rout = 3.8, 1.05503, 0.01288
+    sigma = golden_sigma("laplace_G3.8")
+    R, Lx, Ly, W, Ca, Uw = 8.0, 48, 48, 32, 0.1, 0.05
+    gdot = 2 * Uw / W
+    eta = Ca * sigma / (gdot * R)
+    tem = R * eta / sigma
+    p = dict(Lx=Lx, Ly=Ly, Lz=W, Uw=Uw, G=G, eta_M=eta, rho_in=rin, rho_out=rout)
+    rho = synth.droplet_densities(Lx, Ly, W, R, rho_in=rin, rho_out=rout, noise=0.0, center_offset=False)
+    o = O.Oracle(p, rho)
+    # equilibrium populations of the linear Couette profile u_x(z) (input only)
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    ux = Uw * (2 * (np.arange(W) + 0.5) / W - 1)
+    cu = CX[:, None] * ux[None, :]
+    feq = w[:, None] * (1 + 3 * cu + 4.5 * cu ** 2 - 1.5 * ux[None, :] ** 2)
+    for s in range(2):
+        o.f[s] = feq[:, :, None, None] * rho[s][None]
+    o.step(int(round(9 * tem)))
+    ob = o.observables()
+    D_taylor = Ca * 35 / 32
+    assert abs(ob["D"] / D_taylor - 1) < 0.15, (ob["D"], D_taylor)
+    assert abs(ob["theta_deg"] - 45.0) < 5.0, ob["theta_deg"]
+    assert ob["broken"] == 0 and ob["fragments"] == 1

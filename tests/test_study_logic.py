@@ -38,7 +38,7 @@ def test_bisection_brackets_threshold(fake_runs):
     for s in searches:
         th = fake_threshold(study._case(s.triple, 0.0, 0))
         assert s.lo <= th < s.hi and s.width <= 0.02
-    # 2 checks + ceil(log2(1.7 / 0.02)) = 7 halvings per triple
+    # 2 checks + ceil(log2((CA_MAX - CA_MIN) / 0.02)) = 7 halvings per triple
     assert all(s.runs == 9 for s in searches)
     assert stats["rounds"] == 8
 
@@ -51,7 +51,7 @@ class FakeNetwork:
         self.offset = offset
 
     def forward(self, X):
-        ca = X[:, 0] * 0.6 + 1.2
+        ca = X[:, 0] * study.CA_HALF + study.CA_MID
         cases = [study.Case(Ca=0.0, De=float(x[1] + 1.0), lam=float(np.exp(x[2] * np.log(2.0))),
                             conf=float(x[3] * 0.1 + 0.7), phase=1 if x[5] < 0 else 2) for x in X]
         th = np.array([fake_threshold(c) for c in cases]) + self.offset
@@ -81,7 +81,7 @@ def test_proposal_saves_runs_when_close(fake_runs):
 
 
 def test_features_scaling():
-    c = study.Case(Ca=1.2, De=1.0, lam=1.0, conf=0.7, L2=200.0, phase=1)
+    c = study.Case(Ca=study.CA_MID, De=1.0, lam=1.0, conf=0.7, L2=200.0, phase=1)
     x = study.features([c])[0]
     assert np.allclose(x, [0, 0, 0, 0, 0, -1], atol=1e-6)
 
@@ -111,3 +111,25 @@ def test_autotune_candidates():
     adv = {(k, ty) for k, ty, _ in autotune.candidates([replace(p, advection=1)])}
     assert adv == {(0, 8)}
     assert autotune._key([p], "gpu") != autotune._key([replace(p, advection=1)], "gpu")
+
+
+def test_training_cases_cover_the_transition():
+    """Seven in ten training cases are matrix-viscoelastic with Ca in the
+    upper three quarters of the range; the others span the whole range; all
+    lie inside [CA_MIN, CA_MAX] with confinements in [CONF_MIN, CONF_MAX]."""
+    cs = study.sample_cases(2000, seed=100)
+    mv = [c for c in cs if c.phase == 2]
+    assert 0.65 < len(mv) / len(cs) < 0.75
+    assert all(c.De > 0 for c in mv)
+    lo = study.CA_MIN + 0.25 * (study.CA_MAX - study.CA_MIN)
+    assert all(lo <= c.Ca <= study.CA_MAX for c in mv)
+    assert all(study.CA_MIN <= c.Ca <= study.CA_MAX and study.CONF_MIN <= c.conf <= study.CONF_MAX for c in cs)
+
+
+def test_held_out_triples_are_not_training_cases():
+    from paper_1411_2181_gb300 import study_run
+    tr = study_run.held_out_triples(16)
+    assert len(set(tr)) == 16
+    assert all(t[3] == 2 and t[0] in (1.0, 1.5, 2.0) for t in tr)
+    seen = {(c.De, c.lam, round(c.conf, 6), c.phase) for c in study.sample_cases(2000, seed=100)}
+    assert not any((t[0], t[1], round(t[2], 6), t[3]) in seen for t in tr)
