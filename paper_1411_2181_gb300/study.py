@@ -62,7 +62,7 @@ CA_MID, CA_HALF = 1.4, 0.8         # network input scaling of Ca
 UW = 0.08
 CONF_MIN, CONF_MAX = 0.6, 0.8
 LAMBDAS = (0.5, 1.0)
-T_MAX_TEM = 20.0      # simulated time in emulsion times
+T_MAX_TEM = 30.0      # simulated time in emulsion times
 OBS_EVERY_TEM = 0.5
 
 
