@@ -196,6 +196,29 @@ lbfe_status lbfe_check(lbfe_handle *h);
 lbfe_status lbfe_get_field(lbfe_handle *h, int k, int which, void *host_dst, size_t bytes);
 lbfe_status lbfe_set_field(lbfe_handle *h, int k, int which, const void *host_src, size_t bytes);
 
+/* Column blocks of an instance, for a domain split along x (not in the
+ * paper, whose lattices fit one machine; it gives the way to larger
+ * lattices over several GPUs).  A block is the stored current state of the
+ * x-columns [x0, x0 + nx): populations [38][Lz][Ly][nx] in the storage type
+ * (FP32, or the FP16 / BF16 offsets), conformation [6][Lz][Ly][nx] FP32 and,
+ * in the reduced forms, the per-cell offset densities [Lz][Ly][nx] as FP32
+ * pairs, contiguous in that order, copied bit for bit.  A slab that
+ * carries two ghost columns on each side, filled before every step with the
+ * neighbouring slabs' edge columns, advances its interior columns exactly
+ * as the undivided lattice does: every stencil of the step (Shan-Chen
+ * force, polymer-stress divergence, velocity gradient, streaming) reaches
+ * at most two cells, and the ghosts' own results are discarded.
+ *   lbfe_columns_bytes  size of a block of nx columns of instance k;
+ *   lbfe_get_columns    copy columns [x0, x0 + nx) into the device buffer
+ *                       dev_dst (device to device, asynchronous on the
+ *                       handle's stream);
+ *   lbfe_set_columns    copy a block from dev_src into columns [x0, x0 + nx).
+ * BAD_PARAM for columns outside [0, Lx) or a null pointer, STATE before
+ * lbfe_init.  The buffers are the caller's (at least lbfe_columns_bytes). */
+lbfe_status lbfe_columns_bytes(const lbfe_handle *h, int k, int nx, size_t *bytes);
+lbfe_status lbfe_get_columns(lbfe_handle *h, int k, int x0, int nx, void *dev_dst);
+lbfe_status lbfe_set_columns(lbfe_handle *h, int k, int x0, int nx, const void *dev_src);
+
 /* Number of kernel launches one lbfe_step(h, 1) enqueues: one per group of
  * up to 64 instances (the step kernel carries the instance descriptors in
  * its parameter space). */

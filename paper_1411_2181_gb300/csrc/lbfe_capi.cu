@@ -597,6 +597,59 @@ lbfe_status lbfe_set_field(lbfe_handle *h, int k, int which, const void *host_sr
 
 int lbfe_launches_per_step(const lbfe_handle *h) { return h ? lbfe::fused_launches(h->n) : 0; }
 
+// Column blocks (x-split domain decomposition): the stored state of
+// x-columns [x0, x0 + nx) as [38][Lz][Ly][nx] populations in the storage
+// type, [6][Lz][Ly][nx] FP32 conformation and, in the reduced forms,
+// [Lz][Ly][nx] offset-density pairs; copied as stored, so that a block moved
+// between instances keeps every bit.
+static size_t column_bytes(const lbfe_handle *h, const InstDev &I, int nx) {
+    const size_t cells = (size_t)nx * I.Ly * I.Lz;
+    return cells * (2 * lbfe::Q * elem_bytes(h->precision) + 6 * sizeof(float) +
+                    (h->precision == LBFE_FP32 ? 0 : sizeof(float2)));
+}
+
+lbfe_status lbfe_columns_bytes(const lbfe_handle *h, int k, int nx, size_t *bytes) {
+    if (!h || k < 0 || k >= h->n || !bytes || nx < 1 || nx > h->inst[k].Lx) return LBFE_ERR_BAD_PARAM;
+    *bytes = column_bytes(h, h->inst[k], nx);
+    return LBFE_OK;
+}
+
+static lbfe_status copy_columns(lbfe_handle *h, int k, int x0, int nx, char *dev, bool get) {
+    if (!h || k < 0 || k >= h->n || !dev || nx < 1 || x0 < 0) return LBFE_ERR_BAD_PARAM;
+    const InstDev &I = h->inst[k];
+    if (x0 + nx > I.Lx) return LBFE_ERR_BAD_PARAM;
+    if (!h->ready[k]) return LBFE_ERR_STATE;
+    const size_t rows = (size_t)I.Ly * I.Lz, S = (size_t)I.S;
+    const size_t eb = elem_bytes(h->precision);
+    auto copy = [&](char *field, size_t esz, size_t count, size_t fstride, size_t &off) -> cudaError_t {
+        for (size_t a = 0; a < count; ++a) {
+            char *f = field + (a * fstride + (size_t)x0) * esz;
+            char *b = dev + off;
+            const cudaError_t e =
+                get ? cudaMemcpy2DAsync(b, nx * esz, f, I.Lx * esz, nx * esz, rows, cudaMemcpyDeviceToDevice, h->stream)
+                    : cudaMemcpy2DAsync(f, I.Lx * esz, b, nx * esz, nx * esz, rows, cudaMemcpyDeviceToDevice, h->stream);
+            if (e != cudaSuccess) return e;
+            off += rows * nx * esz;
+        }
+        return cudaSuccess;
+    };
+    size_t off = 0;
+    // the current state: populations f[cur], conformation C[cur] and the
+    // offsets the populations are stored against (dens[cur ^ 1])
+    CK(copy((char *)I.f[h->cur], eb, 2 * lbfe::Q, S, off));
+    CK(copy((char *)I.C[h->cur], sizeof(float), 6, S, off));
+    if (h->precision != LBFE_FP32 && I.dens[0]) CK(copy((char *)I.dens[h->cur ^ 1], sizeof(float2), 1, 0, off));
+    return LBFE_OK;
+}
+
+lbfe_status lbfe_get_columns(lbfe_handle *h, int k, int x0, int nx, void *dev_dst) {
+    return copy_columns(h, k, x0, nx, (char *)dev_dst, true);
+}
+
+lbfe_status lbfe_set_columns(lbfe_handle *h, int k, int x0, int nx, const void *dev_src) {
+    return copy_columns(h, k, x0, nx, (char *)const_cast<void *>(dev_src), false);
+}
+
 lbfe_status lbfe_test_inject(lbfe_handle *h, unsigned what) {
     if (!h || (what & ~(unsigned)LBFE_INJECT_SHORT_COPIES)) return LBFE_ERR_BAD_PARAM;
     CK(cudaStreamSynchronize(h->stream));

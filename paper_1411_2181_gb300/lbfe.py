@@ -84,6 +84,12 @@ _lib.lbfe_load.argtypes = [_H, ct.c_int, ct.c_char_p]
 _lib.lbfe_load.restype = ct.c_int
 _lib.lbfe_crc32.argtypes = [ct.c_void_p, ct.c_size_t, ct.c_uint]
 _lib.lbfe_crc32.restype = ct.c_uint
+_lib.lbfe_columns_bytes.argtypes = [_H, ct.c_int, ct.c_int, ct.POINTER(ct.c_size_t)]
+_lib.lbfe_columns_bytes.restype = ct.c_int
+_lib.lbfe_get_columns.argtypes = [_H, ct.c_int, ct.c_int, ct.c_int, ct.c_void_p]
+_lib.lbfe_get_columns.restype = ct.c_int
+_lib.lbfe_set_columns.argtypes = [_H, ct.c_int, ct.c_int, ct.c_int, ct.c_void_p]
+_lib.lbfe_set_columns.restype = ct.c_int
 _lib.lbfe_observables_noalloc.argtypes = [_P, ct.c_void_p, ct.c_longlong, ct.POINTER(CObs), ct.c_void_p]
 _lib.lbfe_observables_noalloc.restype = ct.c_int
 for _fn in ("lbfe_derive", "lbfe_required_bytes", "lbfe_create", "lbfe_init", "lbfe_step",
@@ -226,6 +232,19 @@ class Solver:
     def test_inject(self, what: int):
         """Test hook of the step kernel's failure path (lbfe_test_inject)."""
         _check(_lib.lbfe_test_inject(self._h, int(what)), "lbfe_test_inject")
+
+    def columns_bytes(self, k: int, nx: int) -> int:
+        nb = ct.c_size_t()
+        _check(_lib.lbfe_columns_bytes(self._h, int(k), int(nx), ct.byref(nb)), "lbfe_columns_bytes")
+        return nb.value
+
+    def get_columns(self, k: int, x0: int, nx: int, dev_ptr: int):
+        """Stored state of x-columns [x0, x0 + nx) into a device buffer (lbfe_get_columns)."""
+        _check(_lib.lbfe_get_columns(self._h, int(k), int(x0), int(nx), ct.c_void_p(dev_ptr)), "lbfe_get_columns")
+
+    def set_columns(self, k: int, x0: int, nx: int, dev_ptr: int):
+        """A column block from a device buffer into x-columns [x0, x0 + nx) (lbfe_set_columns)."""
+        _check(_lib.lbfe_set_columns(self._h, int(k), int(x0), int(nx), ct.c_void_p(dev_ptr)), "lbfe_set_columns")
 
     def _shape(self, k, which):
         p = self.params[k]
