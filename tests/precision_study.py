@@ -1,0 +1,76 @@
+"""Errors of the reduced storage forms against the FP64 oracle over a long
+run (test infrastructure: it runs the oracle).
+
+The 64^3 reduced run of the strongly confined viscoelastic-droplet workload
+(R = 22, W = 64, lambda = 3, De = 2, L^2 = 400) is advanced for --steps
+steps by the CUDA path in FP32, FP16- and BF16-offset storage and by the
+FP64 oracle, with the observables every --every steps; the script prints,
+per storage form, the largest differences from the oracle in D, theta and
+each component's mass, as one JSON document.
+
+    python -m tests.precision_study --steps 10000 --every 500 --out precision.json
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--every", type=int, default=500)
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args(argv)
+    from dataclasses import replace
+
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_1411_2181_gb300 import build, configs
+    build.build()
+    from paper_1411_2181_gb300 import lbfe
+    p, rho, _ = configs.config3(crop=True)
+    traj = {}
+    for prec in (0, 1, 2):
+        s = lbfe.Solver(replace(p, precision=prec))
+        s.init(0, rho)
+        out = [s.observables(0)]
+        for _ in range(a.steps // a.every):
+            s.step(a.every)
+            out.append(s.observables(0))
+        traj[prec] = out
+        s.close()
+    t0 = time.time()
+    o = O.Oracle(p.oracle_dict(), rho)
+    ref = [o.observables()]
+    for _ in range(a.steps // a.every):
+        o.step(a.every)
+        ref.append(o.observables())
+    oracle_s = time.time() - t0
+    rep = {"workload": "droplet_ve 64^3 crop (R 22, W 64, lambda 3, De 2, L2 400)", "steps": a.steps,
+           "every": a.every, "oracle_seconds": oracle_s, "final_oracle": {"D": ref[-1]["D"],
+                                                                         "theta_deg": ref[-1]["theta_deg"]}}
+    for prec, name in ((0, "fp32"), (1, "fp16"), (2, "bf16")):
+        g = traj[prec]
+        rep[name] = {
+            "max_abs_dD": max(abs(x["D"] - y["D"]) for x, y in zip(g, ref)),
+            "max_abs_dtheta_deg": max(abs(x["theta_deg"] - y["theta_deg"]) for x, y in zip(g[1:], ref[1:])),
+            "max_rel_mass_error": max(float((np.abs(np.array(x["mass"]) - np.array(y["mass"])) /
+                                             np.array(y["mass"])).max()) for x, y in zip(g, ref)),
+            "final_D": g[-1]["D"], "final_theta_deg": g[-1]["theta_deg"]}
+    txt = json.dumps(rep, indent=1)
+    print(txt)
+    if a.out:
+        with open(a.out, "w") as fh:
+            fh.write(txt)
+
+
+if __name__ == "__main__":
+    main()

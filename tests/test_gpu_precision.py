@@ -33,18 +33,45 @@ def trajectory(L, prec, steps, every):
     return out
 
 
+STEPS, EVERY = 3000, 300
+
+
 @pytest.fixture(scope="module")
 def runs(L):
-    return {prec: trajectory(L, prec, 1500, 300) for prec in (0, 1, 2)}
+    return {prec: trajectory(L, prec, STEPS, EVERY) for prec in (0, 1, 2)}
 
 
-def test_fp32_observables_match_oracle(L, runs):
+@pytest.fixture(scope="module")
+def oracle_run():
+    """The FP64 oracle over the same 3000 steps (observables every 300)."""
     p, rho, _ = configs.config3(crop=True)
     o = O.Oracle(p.oracle_dict(), rho)
-    o.step(300)
-    ro = o.observables()
-    g = runs[0][1]
-    assert abs(g["D"] - ro["D"]) < 1e-6 and abs(g["theta_deg"] - ro["theta_deg"]) < 1e-3
+    out = [o.observables()]
+    for _ in range(STEPS // EVERY):
+        o.step(EVERY)
+        out.append(o.observables())
+    return out
+
+
+def test_fp32_observables_match_oracle(runs, oracle_run):
+    for g, ro in zip(runs[0], oracle_run):
+        assert abs(g["D"] - ro["D"]) < 2e-5 and abs(g["theta_deg"] - ro["theta_deg"]) < 5e-3
+        assert ro["volume"] == 0 or abs(g["volume"] / ro["volume"] - 1) < 1e-3
+
+
+@pytest.mark.parametrize("prec,tol_D,tol_theta,tol_mass", [(1, 1e-3, 0.05, 1e-4), (2, 5e-3, 0.5, 1e-3)])
+def test_reduced_storage_against_oracle(runs, oracle_run, prec, tol_D, tol_theta, tol_mass):
+    """The reduced forms against the FP64 oracle over 3000 steps: deformation,
+    orientation and each component's mass (relative to the oracle's, which
+    conserves it to rounding)."""
+    red = runs[prec]
+    dD = max(abs(a["D"] - b["D"]) for a, b in zip(oracle_run, red))
+    dth = max(abs(a["theta_deg"] - b["theta_deg"]) for a, b in zip(oracle_run[1:], red[1:]))
+    dm = max((np.abs(np.array(r["mass"]) - np.array(o["mass"])) / np.array(o["mass"])).max()
+             for r, o in zip(red, oracle_run))
+    print(f"precision {prec} vs oracle, {STEPS} steps: max |dD| {dD:.2e}, max |dtheta| {dth:.3f} deg, "
+          f"mass error {dm:.2e}")
+    assert dD < tol_D and dth < tol_theta and dm < tol_mass
 
 
 @pytest.mark.parametrize("prec,tol_D,tol_theta,tol_mass", [(1, 1e-3, 0.05, 1e-4), (2, 5e-3, 0.5, 1e-3)])
