@@ -174,18 +174,19 @@ def run_batch(cases: list[Case], device=None, stats: dict | None = None) -> list
 DE_TRAIN = (0.0, 0.5, 1.0, 1.5, 2.0)
 
 
-def sample_cases(n: int, seed: int) -> list[Case]:
-    """Training cases.  Seven in ten are matrix-viscoelastic with Ca in the
-    upper part of the range (where their break-up happens at this
-    resolution: the network's logit must cross there); the rest cover
-    Newtonian and droplet-viscoelastic droplets over the whole range (stable
-    there)."""
+def sample_cases(n: int, seed: int, mv_ca_from: float | None = None) -> list[Case]:
+    """Training cases.  Seven in ten are matrix-viscoelastic, with Ca
+    uniform from mv_ca_from (default CA_MIN) to CA_MAX: their break-up
+    happens inside the range at this resolution, where the network's logit
+    must cross; the rest cover Newtonian and droplet-viscoelastic droplets
+    over the whole range (stable there)."""
     rng = np.random.default_rng(seed)
+    lo_mv = CA_MIN if mv_ca_from is None else mv_ca_from
     cs = []
     for k in range(n):
         mv = rng.uniform() < 0.7
         if mv:
-            ca = rng.uniform(CA_MIN + 0.25 * (CA_MAX - CA_MIN), CA_MAX)
+            ca = rng.uniform(lo_mv, CA_MAX)
             De, phase = float(rng.choice(DE_TRAIN[1:])), 2
         else:
             ca = rng.uniform(CA_MIN, CA_MAX)
@@ -196,11 +197,12 @@ def sample_cases(n: int, seed: int) -> list[Case]:
     return cs
 
 
-def training_set(n: int, seed: int = 100, batch: int = 64, device=None, stats=None, progress=None):
+def training_set(n: int, seed: int = 100, batch: int = 64, device=None, stats=None, progress=None,
+                 mv_ca_from: float | None = None):
     """Simulate n sampled cases; batches hold cases of similar Ca (similar
     emulsion times, so that few steps go to cases already finished).
     Returns the cases and verdicts of the runs that did not blow up."""
-    cases = sorted(sample_cases(n, seed), key=lambda c: c.Ca)
+    cases = sorted(sample_cases(n, seed, mv_ca_from), key=lambda c: c.Ca)
     verdicts = []
     for s in range(0, n, batch):
         verdicts += run_batch(cases[s:s + batch], device=device, stats=stats)

@@ -63,7 +63,7 @@ def _case_json(c, v):
             "t_break": None if v.t_break != v.t_break else float(v.t_break), "ok": bool(v.ok)}
 
 
-def collect(n: int, seed: int, out: str, batch: int = 64):
+def collect(n: int, seed: int, out: str, batch: int = 64, mv_ca_from: float | None = None):
     """Simulate n training cases; one JSON line per run (written per batch)."""
     stats = {}
     t0 = time.perf_counter()
@@ -76,7 +76,7 @@ def collect(n: int, seed: int, out: str, batch: int = 64):
         written[0] = len(verdicts)
 
     open(out, "w").close()
-    study.training_set(n, seed=seed, batch=batch, stats=stats, progress=progress)
+    study.training_set(n, seed=seed, batch=batch, stats=stats, progress=progress, mv_ca_from=mv_ca_from)
     stats["wall_seconds"] = time.perf_counter() - t0
     print(json.dumps({"collected": written[0], "seed": seed, "stats": stats}))
     return stats
@@ -198,6 +198,8 @@ def main(argv=None):
     c.add_argument("--n", type=int, default=512)
     c.add_argument("--seed", type=int, default=100)
     c.add_argument("--out", required=True)
+    c.add_argument("--mv-ca-from", type=float, default=None,
+                   help="lower end of the matrix-viscoelastic cases' Ca (default: the search range's)")
     t = sub.add_parser("train")
     t.add_argument("--data", required=True, help="comma-separated collect outputs")
     t.add_argument("--epochs", type=int, default=1500)
@@ -213,7 +215,7 @@ def main(argv=None):
     r.add_argument("--lam", type=float, default=1.0)
     a = ap.parse_args(argv)
     if a.cmd == "collect":
-        return collect(a.n, a.seed, a.out)
+        return collect(a.n, a.seed, a.out, mv_ca_from=a.mv_ca_from)
     if a.cmd == "train":
         return train(a.data.split(","), a.epochs, a.params_out)
     if a.cmd == "search":
