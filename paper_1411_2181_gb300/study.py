@@ -251,12 +251,32 @@ def _verdict_round(searches, cas, device, stats, seed):
     return res
 
 
-def _bisect_rounds(searches, tol, device, stats, seed):
+def grid_step(lo: float, hi: float, tol: float) -> float:
+    """Spacing of the Ca values plain bisection of [lo, hi] can visit before
+    its bracket is <= tol wide: (hi - lo) / 2^k with the smallest such k."""
+    return (hi - lo) / 2 ** math.ceil(math.log2((hi - lo) / tol) - 1e-12)
+
+
+def _on_grid(x: float, lo: float, h: float) -> float:
+    return lo + round((x - lo) / h) * h
+
+
+def _bisect_rounds(searches, tol, device, stats, seed, grid=None):
+    """Halve every open bracket until it is <= tol wide.  With a grid
+    (lo, h) the probe is the grid point nearest the bracket's middle, so
+    that brackets on the grid stay on it."""
     while True:
         act = [s for s in searches if s.width > tol + 1e-12]
         if not act:
             return
-        mids = [[0.5 * (s.lo + s.hi)] for s in act]
+        if grid:
+            g0, h = grid
+            mids = []
+            for s in act:
+                k_lo, k_hi = round((s.lo - g0) / h), round((s.hi - g0) / h)
+                mids.append([g0 + ((k_lo + k_hi) // 2) * h])
+        else:
+            mids = [[0.5 * (s.lo + s.hi)] for s in act]
         res = _verdict_round(act, mids, device, stats, seed)
         for s, (m,) in zip(act, mids):
             if res[(id(s), m)]:
@@ -267,7 +287,8 @@ def _bisect_rounds(searches, tol, device, stats, seed):
 
 
 def search_bisect(triples, tol=0.02, lo=CA_MIN, hi=CA_MAX, device=None, seed=7):
-    """Plain bisection: verify the initial bracket, then halve it."""
+    """Plain bisection: verify the initial bracket, then halve it (the
+    midpoints are the grid points lo + k (hi - lo) / 2^n, computed as such)."""
     stats = {}
     searches = [Search(t, lo, hi) for t in triples]
     res = _verdict_round(searches, [[lo, hi]] * len(searches), device, stats, seed)
@@ -277,7 +298,7 @@ def search_bisect(triples, tol=0.02, lo=CA_MIN, hi=CA_MAX, device=None, seed=7):
             s.hi = s.lo = lo          # breaks already at the lower end
         elif not res[(id(s), hi)]:
             s.lo = s.hi = hi          # stable at the upper end
-    _bisect_rounds(searches, tol, device, stats, seed)
+    _bisect_rounds(searches, tol, device, stats, seed, grid=(lo, grid_step(lo, hi, tol)))
     return searches, stats
 
 
@@ -285,8 +306,14 @@ def search_mlp(triples, net, tol=0.02, delta=0.04, lo=CA_MIN, hi=CA_MAX, device=
     """Network-proposed bracket Ca* -/+ delta: both ends are verified by full
     runs; an end that contradicts the bracket (the lower end breaks, or the
     upper end stays stable) becomes the other end and the bracket moves by
-    2 delta in that direction, until both ends hold.  Then it is halved."""
+    2 delta in that direction, until both ends hold.  Then it is halved.
+    Every probe lies on the grid of Ca values plain bisection of [lo, hi]
+    visits (Ca* and delta rounded to it, delta to at least one step), so
+    that where the verdicts are monotone in Ca both searches end on the
+    same grid cell."""
     stats = {"rounds": 0}
+    h = grid_step(lo, hi, tol)
+    delta = max(h, round(delta / h) * h)
     grid = np.linspace(lo, hi, 341)
     searches, ok = [], {}
     for t in triples:
@@ -302,8 +329,8 @@ def search_mlp(triples, net, tol=0.02, delta=0.04, lo=CA_MIN, hi=CA_MAX, device=
             s = Search(t, lo, lo)
             ok[id(s)] = [True, False]
         else:
-            ca_star = float(grid[above[0]])
-            s = Search(t, max(lo, ca_star - delta), min(hi, ca_star + delta))
+            ca_star = _on_grid(float(grid[above[0]]), lo, h)
+            s = Search(t, max(lo, _on_grid(ca_star - delta, lo, h)), min(hi, _on_grid(ca_star + delta, lo, h)))
             ok[id(s)] = [False, False]   # lower end stable / upper end broken verified
         searches.append(s)
     pending = list(searches)
@@ -329,13 +356,13 @@ def search_mlp(triples, net, tol=0.02, delta=0.04, lo=CA_MIN, hi=CA_MAX, device=
                 if s.lo <= lo:
                     s.lo, f[0] = lo, True
                 else:
-                    s.lo, f[0] = max(lo, s.lo - 2 * delta), False
+                    s.lo, f[0] = max(lo, _on_grid(s.lo - 2 * delta, lo, h)), False
             elif r_hi is False:                   # stable at the upper end: Ca_cr is above it
                 s.lo, f[0] = s.hi, True
                 if s.hi >= hi:
                     s.hi, f[1] = hi, True
                 else:
-                    s.hi, f[1] = min(hi, s.hi + 2 * delta), False
+                    s.hi, f[1] = min(hi, _on_grid(s.hi + 2 * delta, lo, h)), False
             else:
                 if r_lo is False:
                     f[0] = True
@@ -344,5 +371,5 @@ def search_mlp(triples, net, tol=0.02, delta=0.04, lo=CA_MIN, hi=CA_MAX, device=
             if not (f[0] and f[1]):
                 nxt.append(s)
         pending = nxt
-    _bisect_rounds(searches, tol, device, stats, seed)
+    _bisect_rounds(searches, tol, device, stats, seed, grid=(lo, h))
     return searches, stats

@@ -133,3 +133,18 @@ def test_held_out_triples_are_not_training_cases():
     assert all(t[3] == 2 and t[0] in (1.0, 1.5, 2.0) for t in tr)
     seen = {(c.De, c.lam, round(c.conf, 6), c.phase) for c in study.sample_cases(2000, seed=100)}
     assert not any((t[0], t[1], round(t[2], 6), t[3]) in seen for t in tr)
+
+
+@pytest.mark.parametrize("offset", [0.0, 0.03, -0.07, 0.2])
+def test_proposal_ends_on_the_bisection_grid_cell(fake_runs, offset):
+    """The proposal's probes lie on bisection's grid of Ca values, so with a
+    monotone verdict both searches end on the same grid cell."""
+    sb, _ = study.search_bisect(TRIPLES, tol=0.02)
+    sm, _ = study.search_mlp(TRIPLES, FakeNetwork(offset), tol=0.02, delta=0.06)
+    h = study.grid_step(study.CA_MIN, study.CA_MAX, 0.02)
+    assert h == pytest.approx(1.6 / 128)
+    for b, m in zip(sb, sm):
+        assert m.lo == pytest.approx(b.lo) and m.hi == pytest.approx(b.hi)
+        for ca, _ in m.history:
+            k = (ca - study.CA_MIN) / h
+            assert abs(k - round(k)) < 1e-9
