@@ -6,9 +6,12 @@ The 64^3 reduced run of the strongly confined viscoelastic-droplet workload
 steps by the CUDA path in FP32, FP16- and BF16-offset storage and by the
 FP64 oracle, with the observables every --every steps; the script prints,
 per storage form, the largest differences from the oracle in D, theta and
-each component's mass, as one JSON document.
+each component's mass, as one JSON document.  With --full-steps N the full
+256 x 128 x 64 lattice of the same workload (beyond the oracle's reach in
+a few minutes) is also advanced N steps in the three forms, and the reduced
+forms are compared with FP32 storage.
 
-    python -m tests.precision_study --steps 10000 --every 500 --out precision.json
+    python -m tests.precision_study --steps 10000 --every 500 --full-steps 10000 --out precision.json
 """
 from __future__ import annotations
 
@@ -26,6 +29,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--every", type=int, default=500)
+    ap.add_argument("--full-steps", type=int, default=0)
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     from dataclasses import replace
@@ -65,11 +69,48 @@ def main(argv=None):
             "max_rel_mass_error": max(float((np.abs(np.array(x["mass"]) - np.array(y["mass"])) /
                                              np.array(y["mass"])).max()) for x, y in zip(g, ref)),
             "final_D": g[-1]["D"], "final_theta_deg": g[-1]["theta_deg"]}
+    if a.full_steps > 0:
+        rep["full"] = full_lattice(a.full_steps, a.every)
     txt = json.dumps(rep, indent=1)
     print(txt)
     if a.out:
         with open(a.out, "w") as fh:
             fh.write(txt)
+
+
+def full_lattice(steps: int, every: int) -> dict:
+    """The full 256 x 128 x 64 lattice in the three storage forms; the
+    reduced forms' largest differences from FP32 storage over the run."""
+    from dataclasses import replace
+
+    import numpy as np
+
+    from paper_1411_2181_gb300 import configs, lbfe
+    p, rho, _ = configs.config3()
+    traj = {}
+    t0 = time.time()
+    for prec in (0, 1, 2):
+        s = lbfe.Solver(replace(p, precision=prec))
+        s.init(0, rho)
+        out = [s.observables(0)]
+        for _ in range(steps // every):
+            s.step(every)
+            out.append(s.observables(0))
+        traj[prec] = (out, s.check())
+        s.close()
+    rep = {"lattice": [p.Lx, p.Ly, p.Lz], "steps": steps, "every": every, "seconds": time.time() - t0,
+           "final_fp32": {"D": traj[0][0][-1]["D"], "theta_deg": traj[0][0][-1]["theta_deg"]},
+           "status": {n: traj[k][1] for k, n in ((0, "fp32"), (1, "fp16"), (2, "bf16"))}}
+    ref = traj[0][0]
+    for prec, name in ((1, "fp16"), (2, "bf16")):
+        g = traj[prec][0]
+        rep[name + "_vs_fp32"] = {
+            "max_abs_dD": max(abs(x["D"] - y["D"]) for x, y in zip(g, ref)),
+            "max_abs_dtheta_deg": max(abs(x["theta_deg"] - y["theta_deg"]) for x, y in zip(g[1:], ref[1:])),
+            "max_rel_mass_error": max(float((np.abs(np.array(x["mass"]) - np.array(y["mass"])) /
+                                             np.array(y["mass"])).max()) for x, y in zip(g, ref)),
+            "final_D": g[-1]["D"], "final_theta_deg": g[-1]["theta_deg"]}
+    return rep
 
 
 if __name__ == "__main__":
