@@ -75,6 +75,7 @@ class Case:
     L2: float = 100.0
     phase: int = 1     # 1 droplet viscoelastic, 2 matrix viscoelastic
     seed: int = 0
+    uw: float = UW     # wall speed (the trend at a second wall speed; the network's cases keep UW)
 
 
 @dataclass
@@ -88,11 +89,11 @@ class Verdict:
 
 
 def case_params(c: Case) -> Params:
-    """Lattice parameters of a case: wall speed UW, eta_M from Ca (Sec. 1),
+    """Lattice parameters of a case: its wall speed, eta_M from Ca (Sec. 1),
     tau_P from De (Eq. 8), emulsion time R eta_M / sigma (Eq. 9)."""
     R = 0.5 * c.conf * W
     return configs.make_params(LX, LY, W, R, Ca=c.Ca, De=c.De, lam=c.lam, beta=0.4, L2=c.L2, phase=c.phase,
-                               Uw=UW, G=G_STUDY, sigma=SIGMA_STUDY, rho_in=RHO_IN_STUDY,
+                               Uw=c.uw, G=G_STUDY, sigma=SIGMA_STUDY, rho_in=RHO_IN_STUDY,
                                rho_out=RHO_OUT_STUDY)
 
 
@@ -232,23 +233,24 @@ class Search:
     hi: float
     runs: int = 0
     history: list = field(default_factory=list)
+    diverged: list = field(default_factory=list)   # Ca values whose run blew up (counted as breaking)
 
     @property
     def width(self):
         return self.hi - self.lo
 
 
-def _case(triple, Ca, seed):
+def _case(triple, Ca, seed, uw=UW):
     De, lam, conf, phase = triple
-    return Case(Ca=Ca, De=De, lam=lam, conf=conf, phase=phase, seed=seed)
+    return Case(Ca=Ca, De=De, lam=lam, conf=conf, phase=phase, seed=seed, uw=uw)
 
 
-def _verdict_round(searches, cas, device, stats, seed):
+def _verdict_round(searches, cas, device, stats, seed, uw=UW):
     """One batched round: a full run for every (search, Ca) pair."""
     pairs = [(s, ca) for s, lst in zip(searches, cas) for ca in lst]
     if not pairs:
         return {}
-    vs = run_batch([_case(s.triple, ca, seed) for s, ca in pairs], device=device, stats=stats)
+    vs = run_batch([_case(s.triple, ca, seed, uw) for s, ca in pairs], device=device, stats=stats)
     res = {}
     for (s, ca), v in zip(pairs, vs):
         s.runs += 1
@@ -257,6 +259,7 @@ def _verdict_round(searches, cas, device, stats, seed):
         br = v.broken or not v.ok
         if not v.ok:
             stats["diverged"] = stats.get("diverged", 0) + 1
+            s.diverged.append(ca)
         s.history.append((ca, br))
         res[(id(s), ca)] = br
     return res
@@ -272,7 +275,7 @@ def _on_grid(x: float, lo: float, h: float) -> float:
     return lo + round((x - lo) / h) * h
 
 
-def _bisect_rounds(searches, tol, device, stats, seed, grid=None):
+def _bisect_rounds(searches, tol, device, stats, seed, grid=None, uw=UW):
     """Halve every open bracket until it is <= tol wide.  With a grid
     (lo, h) the probe is the grid point nearest the bracket's middle, so
     that brackets on the grid stay on it."""
@@ -288,7 +291,7 @@ def _bisect_rounds(searches, tol, device, stats, seed, grid=None):
                 mids.append([g0 + ((k_lo + k_hi) // 2) * h])
         else:
             mids = [[0.5 * (s.lo + s.hi)] for s in act]
-        res = _verdict_round(act, mids, device, stats, seed)
+        res = _verdict_round(act, mids, device, stats, seed, uw)
         for s, (m,) in zip(act, mids):
             if res[(id(s), m)]:
                 s.hi = m
@@ -297,19 +300,19 @@ def _bisect_rounds(searches, tol, device, stats, seed, grid=None):
         stats["rounds"] = stats.get("rounds", 0) + 1
 
 
-def search_bisect(triples, tol=0.02, lo=CA_MIN, hi=CA_MAX, device=None, seed=7):
+def search_bisect(triples, tol=0.02, lo=CA_MIN, hi=CA_MAX, device=None, seed=7, uw=UW):
     """Plain bisection: verify the initial bracket, then halve it (the
     midpoints are the grid points lo + k (hi - lo) / 2^n, computed as such)."""
     stats = {}
     searches = [Search(t, lo, hi) for t in triples]
-    res = _verdict_round(searches, [[lo, hi]] * len(searches), device, stats, seed)
+    res = _verdict_round(searches, [[lo, hi]] * len(searches), device, stats, seed, uw)
     stats["rounds"] = 1
     for s in searches:
         if res[(id(s), lo)]:
             s.hi = s.lo = lo          # breaks already at the lower end
         elif not res[(id(s), hi)]:
             s.lo = s.hi = hi          # stable at the upper end
-    _bisect_rounds(searches, tol, device, stats, seed, grid=(lo, grid_step(lo, hi, tol)))
+    _bisect_rounds(searches, tol, device, stats, seed, grid=(lo, grid_step(lo, hi, tol)), uw=uw)
     return searches, stats
 
 

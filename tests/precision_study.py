@@ -32,34 +32,48 @@ def main(argv=None):
     ap.add_argument("--full-steps", type=int, default=0)
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
+    from paper_1411_2181_gb300 import build
+    build.build()
+    rep = {}
+    if a.steps > 0:
+        rep = crop_against_oracle(a.steps, a.every)
+    if a.full_steps > 0:
+        rep["full"] = full_lattice(a.full_steps, a.every)
+    txt = json.dumps(rep, indent=1)
+    print(txt)
+    if a.out:
+        with open(a.out, "w") as fh:
+            fh.write(txt)
+
+
+def crop_against_oracle(steps: int, every: int) -> dict:
+    """The 64^3 crop in the three storage forms against the FP64 oracle."""
     from dataclasses import replace
 
     import numpy as np
 
     from oracle import oracle as O
-    from paper_1411_2181_gb300 import build, configs
-    build.build()
-    from paper_1411_2181_gb300 import lbfe
+    from paper_1411_2181_gb300 import configs, lbfe
     p, rho, _ = configs.config3(crop=True)
     traj = {}
     for prec in (0, 1, 2):
         s = lbfe.Solver(replace(p, precision=prec))
         s.init(0, rho)
         out = [s.observables(0)]
-        for _ in range(a.steps // a.every):
-            s.step(a.every)
+        for _ in range(steps // every):
+            s.step(every)
             out.append(s.observables(0))
         traj[prec] = out
         s.close()
     t0 = time.time()
     o = O.Oracle(p.oracle_dict(), rho)
     ref = [o.observables()]
-    for _ in range(a.steps // a.every):
-        o.step(a.every)
+    for _ in range(steps // every):
+        o.step(every)
         ref.append(o.observables())
     oracle_s = time.time() - t0
-    rep = {"workload": "droplet_ve 64^3 crop (R 22, W 64, lambda 3, De 2, L2 400)", "steps": a.steps,
-           "every": a.every, "oracle_seconds": oracle_s, "final_oracle": {"D": ref[-1]["D"],
+    rep = {"workload": "droplet_ve 64^3 crop (R 22, W 64, lambda 3, De 2, L2 400)", "steps": steps,
+           "every": every, "oracle_seconds": oracle_s, "final_oracle": {"D": ref[-1]["D"],
                                                                          "theta_deg": ref[-1]["theta_deg"]}}
     for prec, name in ((0, "fp32"), (1, "fp16"), (2, "bf16")):
         g = traj[prec]
@@ -69,13 +83,7 @@ def main(argv=None):
             "max_rel_mass_error": max(float((np.abs(np.array(x["mass"]) - np.array(y["mass"])) /
                                              np.array(y["mass"])).max()) for x, y in zip(g, ref)),
             "final_D": g[-1]["D"], "final_theta_deg": g[-1]["theta_deg"]}
-    if a.full_steps > 0:
-        rep["full"] = full_lattice(a.full_steps, a.every)
-    txt = json.dumps(rep, indent=1)
-    print(txt)
-    if a.out:
-        with open(a.out, "w") as fh:
-            fh.write(txt)
+    return rep
 
 
 def full_lattice(steps: int, every: int) -> dict:
