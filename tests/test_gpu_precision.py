@@ -103,3 +103,33 @@ def test_reduced_storage_launch_shapes_agree(L, prec):
     scale = np.abs(ref).max()
     for f in out[1:]:
         assert np.abs(f - ref).max() <= (2e-3 if prec == 1 else 2e-2) * scale
+
+
+def test_full_lattice_reduced_storage_10k_steps(L):
+    """The full 256 x 128 x 64 lattice of the workload over its 10^4 steps
+    (beyond the oracle's reach in the suite): FP16 storage keeps the
+    deformation within 1e-3 of FP32 storage, the bound the reduced form is
+    held to; BF16 (8-bit mantissa) is held to the looser bounds its measured
+    errors set (max |dD| 8.3e-3, |dtheta| 0.49 deg, relative mass 1.6e-2)."""
+    p, rho, _ = configs.config3()
+    steps, every = 10000, 500
+    traj = {}
+    for prec in (0, 1, 2):
+        s = L.Solver(replace(p, precision=prec))
+        s.init(0, rho)
+        out = [s.observables(0)]
+        for _ in range(steps // every):
+            s.step(every)
+            out.append(s.observables(0))
+        assert s.check() == L.OK
+        traj[prec] = out
+        s.close()
+    for prec, tol_D, tol_theta, tol_mass in ((1, 1e-3, 0.1, 1e-3), (2, 2e-2, 1.0, 3e-2)):
+        ref, red = traj[0], traj[prec]
+        dD = max(abs(a["D"] - b["D"]) for a, b in zip(ref, red))
+        dth = max(abs(a["theta_deg"] - b["theta_deg"]) for a, b in zip(ref[1:], red[1:]))
+        dm = max((np.abs(np.array(r["mass"]) - np.array(f["mass"])) / np.array(f["mass"])).max()
+                 for r, f in zip(red, ref))
+        print(f"full lattice, precision {prec} vs FP32, {steps} steps: max |dD| {dD:.2e}, "
+              f"max |dtheta| {dth:.3f} deg, mass {dm:.2e}")
+        assert dD < tol_D and dth < tol_theta and dm < tol_mass, (prec, dD, dth, dm)
