@@ -339,7 +339,7 @@ def time_form(name: str, prec: int, steps: int, warmup: int, device: str, autotu
 # forms, and the 64-instance uneven batch in one persistent launch per step
 FORMS = [("matrix_ve_192x96x80", 1), ("matrix_ve_192x96x80", 2),
          ("droplet_ve_256x128x64", 0), ("droplet_ve_256x128x64", 1), ("droplet_ve_256x128x64", 2),
-         ("batched_64", 0)]
+         ("batched_64", 0), ("batched_64", 1)]
 
 
 def run_ours(a):
