@@ -126,13 +126,18 @@ k_fused(const __grid_constant__ StepArgs A) {
         for (int r = 0; r < MH; ++r) {
             int gx, gy;
             ring2_coord<TY>(min(t + r * NT, Gm::NRING2 - 1), gx, gy);
-            h_on[r] = (r + 1) * NT <= Gm::NRING2 || t + r * NT < Gm::NRING2;
             h_ofs[r] = s_rows[gy] + s_cols[gx];
             h_idx[r] = gy * RX + gx;
             h_gx[r] = gx;
             h_gy[r] = gy;
             const int xg = x0 + gx, yg = y0 + gy;
             h_dom[r] = xg >= 0 && xg < Lx && yg >= 0 && yg < Ly;
+            // a halo cell more than two cells past the upper x or y edge of
+            // the lattice (in a tile the edge cuts) is read by no valid cell:
+            // every stencil of the step reaches two cells.  It is neither
+            // loaded nor stored; its ring slots keep values only cells whose
+            // results are discarded read
+            h_on[r] = ((r + 1) * NT <= Gm::NRING2 || t + r * NT < Gm::NRING2) && xg < Lx + 2 && yg < Ly + 2;
         }
 
         // this thread has a halo cell staged in the region copy
