@@ -148,3 +148,24 @@ def test_proposal_ends_on_the_bisection_grid_cell(fake_runs, offset):
         for ca, _ in m.history:
             k = (ca - study.CA_MIN) / h
             assert abs(k - round(k)) < 1e-9
+
+
+def test_bisection_at_another_wall_speed_and_range(monkeypatch):
+    """The trend's second wall speed reaches every case of the search, and
+    the search range follows its upper end."""
+    seen = []
+
+    def run_batch(cases, device=None, stats=None):
+        seen.extend(c.uw for c in cases)
+        return [study.Verdict(c.Ca > 2.45, 0.1, 30.0, 0, float("nan")) for c in cases]
+
+    monkeypatch.setattr(study, "run_batch", run_batch)
+    searches, _ = study.search_bisect([(0.0, 1.0, 0.7, 1)], tol=0.02, hi=2.7, uw=0.098)
+    s = searches[0]
+    assert seen and all(u == 0.098 for u in seen)
+    assert s.lo <= 2.45 < s.hi and s.width <= 0.02
+    p = study.case_params(study._case(s.triple, 2.0, 0, uw=0.098))
+    p0 = study.case_params(study._case(s.triple, 2.0, 0))
+    # the same Ca at a higher wall speed: the same viscosity times shear
+    # rate, so a proportionally smaller matrix viscosity
+    assert p.Uw == 0.098 and abs(p.eta_M * 0.098 - p0.eta_M * study.UW) < 1e-12
