@@ -169,3 +169,18 @@ def test_bisection_at_another_wall_speed_and_range(monkeypatch):
     # the same Ca at a higher wall speed: the same viscosity times shear
     # rate, so a proportionally smaller matrix viscosity
     assert p.Uw == 0.098 and abs(p.eta_M * 0.098 - p0.eta_M * study.UW) < 1e-12
+
+
+def test_blown_up_runs_count_as_breaking_and_are_listed(monkeypatch):
+    """A run that blows up gives no verdict: the search treats it as
+    breaking and lists its Ca, so a report can show which brackets rest on
+    one."""
+    def run_batch(cases, device=None, stats=None):
+        return [study.Verdict(c.Ca > 1.5, 0.1, 30.0, 0, float("nan"), ok=c.Ca < 2.0) for c in cases]
+
+    monkeypatch.setattr(study, "run_batch", run_batch)
+    searches, stats = study.search_bisect([(2.0, 1.0, 0.7, 2)], tol=0.02)
+    s = searches[0]
+    assert s.diverged == [study.CA_MAX] and stats["diverged"] == 1
+    assert (study.CA_MAX, True) in s.history
+    assert s.lo <= 1.5 < s.hi and s.width <= 0.02
