@@ -96,18 +96,66 @@ def config_dict(name, ps):
 
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """SM clock and clock-event reasons of the benchmark's GPU while the
+    timed region runs: read through NVML (read-only queries) on entry, every
+    0.5 ms and on exit, the GPU found by its UUID; where NVML cannot be loaded, nvidia-smi every
+    200 ms from 0.3 s before the region to 0.25 s after it."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits
+    REASON_BITS = ((0x4, "sw_power_cap"), (0x8, "hw_slowdown"), (0x20, "sw_thermal_slowdown"),
+                   (0x40, "hw_thermal_slowdown"), (0x80, "hw_power_brake_slowdown"))
 
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
         self.lines = []
+        self.nvml = None
+        self.samples = []
+        self.max_mhz = None
+        self.stop = threading.Event()
+
+    def _nvml_open(self):
+        import ctypes as ct
+        import torch
+        lib = ct.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            return None
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(self.idx).uuid)
+        dev = ct.c_void_p()
+        if lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ct.byref(dev)) != 0:
+            return None
+        mx = ct.c_uint()
+        if lib.nvmlDeviceGetMaxClockInfo(dev, 1, ct.byref(mx)) == 0:   # 1: NVML_CLOCK_SM
+            self.max_mhz = float(mx.value)
+        reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        return lib, dev, reasons
+
+    def _nvml_sample(self):
+        import ctypes as ct
+        lib, dev, reasons = self.nvml
+        clk, bits = ct.c_uint(), ct.c_ulonglong()
+        if lib.nvmlDeviceGetClockInfo(dev, 1, ct.byref(clk)) == 0 and reasons(dev, ct.byref(bits)) == 0:
+            self.samples.append((float(clk.value), int(bits.value)))
+
+    def _nvml_loop(self):
+        while not self.stop.is_set():
+            self._nvml_sample()
+            time.sleep(0.0005)
 
     def __enter__(self):
+        try:
+            self.nvml = self._nvml_open()
+        except Exception:
+            self.nvml = None
+        if self.nvml:
+            self._nvml_sample()
+            self.t = threading.Thread(target=self._nvml_loop, daemon=True)
+            self.t.start()
+            return self
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -124,6 +172,14 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def __exit__(self, *a):
+        if self.nvml:
+            self.stop.set()
+            self.t.join(1.0)
+            try:
+                self._nvml_sample()
+            except Exception:
+                pass
+            return False
         if self.proc:
             time.sleep(0.25)
             self.proc.terminate()
@@ -131,8 +187,16 @@ class ClockSampler:
                 self.proc.wait(2)
             except Exception:
                 self.proc.kill()
+        return False
 
     def summary(self):
+        if self.nvml is not None:
+            if not self.samples:
+                return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unsampled"], "samples": 0,
+                        "sampler": "nvml"}
+            reasons = {nm for bit, nm in self.REASON_BITS for _, b in self.samples if b & bit}
+            return {"sm_mhz": statistics.median(c for c, _ in self.samples), "sm_max_mhz": self.max_mhz,
+                    "reasons": sorted(reasons), "samples": len(self.samples), "sampler": "nvml, 0.5 ms"}
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
@@ -150,7 +214,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "sampler": "nvidia-smi, 200 ms"}
 
 
 # ---------------------------------------------------------------- roofline inputs
