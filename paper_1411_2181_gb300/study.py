@@ -76,6 +76,7 @@ class Case:
     phase: int = 1     # 1 droplet viscoelastic, 2 matrix viscoelastic
     seed: int = 0
     uw: float = UW     # wall speed (the trend at a second wall speed; the network's cases keep UW)
+    w: int = W         # gap; the box scales with it (the trend at a finer resolution)
 
 
 @dataclass
@@ -91,8 +92,9 @@ class Verdict:
 def case_params(c: Case) -> Params:
     """Lattice parameters of a case: its wall speed, eta_M from Ca (Sec. 1),
     tau_P from De (Eq. 8), emulsion time R eta_M / sigma (Eq. 9)."""
-    R = 0.5 * c.conf * W
-    return configs.make_params(LX, LY, W, R, Ca=c.Ca, De=c.De, lam=c.lam, beta=0.4, L2=c.L2, phase=c.phase,
+    R = 0.5 * c.conf * c.w
+    lx, ly = (LX, LY) if c.w == W else (int(round(LX * c.w / W / 8)) * 8, int(round(LY * c.w / W / 4)) * 4)
+    return configs.make_params(lx, ly, c.w, R, Ca=c.Ca, De=c.De, lam=c.lam, beta=0.4, L2=c.L2, phase=c.phase,
                                Uw=c.uw, G=G_STUDY, sigma=SIGMA_STUDY, rho_in=RHO_IN_STUDY,
                                rho_out=RHO_OUT_STUDY)
 
@@ -240,17 +242,17 @@ class Search:
         return self.hi - self.lo
 
 
-def _case(triple, Ca, seed, uw=UW):
+def _case(triple, Ca, seed, **case_kw):
     De, lam, conf, phase = triple
-    return Case(Ca=Ca, De=De, lam=lam, conf=conf, phase=phase, seed=seed, uw=uw)
+    return Case(Ca=Ca, De=De, lam=lam, conf=conf, phase=phase, seed=seed, **case_kw)
 
 
-def _verdict_round(searches, cas, device, stats, seed, uw=UW):
+def _verdict_round(searches, cas, device, stats, seed, case_kw=None):
     """One batched round: a full run for every (search, Ca) pair."""
     pairs = [(s, ca) for s, lst in zip(searches, cas) for ca in lst]
     if not pairs:
         return {}
-    vs = run_batch([_case(s.triple, ca, seed, uw) for s, ca in pairs], device=device, stats=stats)
+    vs = run_batch([_case(s.triple, ca, seed, **(case_kw or {})) for s, ca in pairs], device=device, stats=stats)
     res = {}
     for (s, ca), v in zip(pairs, vs):
         s.runs += 1
@@ -275,7 +277,7 @@ def _on_grid(x: float, lo: float, h: float) -> float:
     return lo + round((x - lo) / h) * h
 
 
-def _bisect_rounds(searches, tol, device, stats, seed, grid=None, uw=UW):
+def _bisect_rounds(searches, tol, device, stats, seed, grid=None, case_kw=None):
     """Halve every open bracket until it is <= tol wide.  With a grid
     (lo, h) the probe is the grid point nearest the bracket's middle, so
     that brackets on the grid stay on it."""
@@ -291,7 +293,7 @@ def _bisect_rounds(searches, tol, device, stats, seed, grid=None, uw=UW):
                 mids.append([g0 + ((k_lo + k_hi) // 2) * h])
         else:
             mids = [[0.5 * (s.lo + s.hi)] for s in act]
-        res = _verdict_round(act, mids, device, stats, seed, uw)
+        res = _verdict_round(act, mids, device, stats, seed, case_kw)
         for s, (m,) in zip(act, mids):
             if res[(id(s), m)]:
                 s.hi = m
@@ -300,19 +302,20 @@ def _bisect_rounds(searches, tol, device, stats, seed, grid=None, uw=UW):
         stats["rounds"] = stats.get("rounds", 0) + 1
 
 
-def search_bisect(triples, tol=0.02, lo=CA_MIN, hi=CA_MAX, device=None, seed=7, uw=UW):
+def search_bisect(triples, tol=0.02, lo=CA_MIN, hi=CA_MAX, device=None, seed=7, **case_kw):
     """Plain bisection: verify the initial bracket, then halve it (the
-    midpoints are the grid points lo + k (hi - lo) / 2^n, computed as such)."""
+    midpoints are the grid points lo + k (hi - lo) / 2^n, computed as such).
+    case_kw: Case fields other than the triple's (wall speed uw, gap w)."""
     stats = {}
     searches = [Search(t, lo, hi) for t in triples]
-    res = _verdict_round(searches, [[lo, hi]] * len(searches), device, stats, seed, uw)
+    res = _verdict_round(searches, [[lo, hi]] * len(searches), device, stats, seed, case_kw)
     stats["rounds"] = 1
     for s in searches:
         if res[(id(s), lo)]:
             s.hi = s.lo = lo          # breaks already at the lower end
         elif not res[(id(s), hi)]:
             s.lo = s.hi = hi          # stable at the upper end
-    _bisect_rounds(searches, tol, device, stats, seed, grid=(lo, grid_step(lo, hi, tol)), uw=uw)
+    _bisect_rounds(searches, tol, device, stats, seed, grid=(lo, grid_step(lo, hi, tol)), case_kw=case_kw)
     return searches, stats
 
 

@@ -159,18 +159,21 @@ def search(params: str, n_triples: int, out: str | None, delta: float = 0.06, tr
     return rep
 
 
-def trend(out=None, lam=1.0, confs=(0.6, 0.7, 0.8), uw=study.UW, ca_max=study.CA_MAX, de=2.0):
+def trend(out=None, lam=1.0, confs=(0.6, 0.7, 0.8), uw=study.UW, ca_max=study.CA_MAX, de=2.0, w=study.W,
+          kinds=("newtonian", "DV", "MV")):
     """Ca_cr (bisection, bracket width 0.02) for Newtonian (De = 0), droplet-
     and matrix-viscoelastic (De = de) droplets at viscosity ratio lam against
     2R/W on the study's domains.  Sec. 3 reports, at the paper's sizes, that
     droplet viscoelasticity raises Ca_cr and matrix viscoelasticity lowers
     it, more so under strong confinement.  A higher wall speed uw reaches a
     higher Ca at the same relaxation times (Ca is proportional to the shear
-    rate), as in the paper's protocol of raising the wall speed."""
-    kinds = (("newtonian", 0.0, 1), ("DV", de, 1), ("MV", de, 2))
+    rate), as in the paper's protocol of raising the wall speed.  A larger
+    gap w (the box scaled with it) resolves the droplet and its interface
+    more finely at the same range of Ca."""
+    kinds = tuple(k for k in (("newtonian", 0.0, 1), ("DV", de, 1), ("MV", de, 2)) if k[0] in kinds)
     triples = [(De, lam, conf, phase) for conf in confs for _, De, phase in kinds]
     t0 = time.perf_counter()
-    sb, st = study.search_bisect(triples, hi=ca_max, uw=uw)
+    sb, st = study.search_bisect(triples, hi=ca_max, uw=uw, w=w)
     rows = {}
     for i, s in enumerate(sb):
         name = kinds[i % len(kinds)][0]
@@ -181,7 +184,9 @@ def trend(out=None, lam=1.0, confs=(0.6, 0.7, 0.8), uw=study.UW, ca_max=study.CA
                                           "diverged_at": sorted(s.diverged)})
     rep = {"lambda": lam, "trend": rows, "runs": st.get("runs", 0), "rounds": st.get("rounds", 0),
            "diverged": st.get("diverged", 0), "seconds": time.perf_counter() - t0,
-           "Ca_range": [study.CA_MIN, ca_max], "Uw": uw, "De": de}
+           "Ca_range": [study.CA_MIN, ca_max], "Uw": uw, "De": de, "W": w,
+           "box": [getattr(study.case_params(study._case(triples[0], 1.0, 0, uw=uw, w=w)), k)
+                   for k in ("Lx", "Ly", "Lz")]}
     _emit(rep, out)
     return rep
 
@@ -219,6 +224,8 @@ def main(argv=None):
     r.add_argument("--uw", type=float, default=study.UW, help="wall speed (lattice units)")
     r.add_argument("--ca-max", type=float, default=study.CA_MAX)
     r.add_argument("--de", type=float, default=2.0, help="Deborah number of the DV and MV droplets")
+    r.add_argument("--w", type=int, default=study.W, help="gap W (the box scales with it)")
+    r.add_argument("--kinds", default="newtonian,DV,MV")
     a = ap.parse_args(argv)
     if a.cmd == "collect":
         return collect(a.n, a.seed, a.out, mv_ca_from=a.mv_ca_from)
@@ -227,7 +234,7 @@ def main(argv=None):
     if a.cmd == "search":
         info = json.load(open(a.train_info)) if a.train_info else None
         return search(a.params, a.triples, a.out, a.delta, info)
-    return trend(a.out, a.lam, uw=a.uw, ca_max=a.ca_max, de=a.de)
+    return trend(a.out, a.lam, uw=a.uw, ca_max=a.ca_max, de=a.de, w=a.w, kinds=tuple(a.kinds.split(",")))
 
 
 if __name__ == "__main__":
