@@ -184,3 +184,20 @@ def test_blown_up_runs_count_as_breaking_and_are_listed(monkeypatch):
     assert s.diverged == [study.CA_MAX] and stats["diverged"] == 1
     assert (study.CA_MAX, True) in s.history
     assert s.lo <= 1.5 < s.hi and s.width <= 0.02
+
+
+def test_cases_at_a_larger_gap():
+    """At another gap W the box scales with it (x and y extents rounded to
+    multiples of 8 and 4), R = (2R/W) W / 2, and a given Ca needs the same
+    matrix viscosity (Ca = eta_M (2 U_w / W) R / sigma, so W cancels at a
+    fixed 2R/W): the relaxation times, and with them the reachable Ca range,
+    do not change with W."""
+    c40 = study.Case(Ca=1.7, De=2.0, lam=1.0, conf=0.7, phase=2)
+    c64 = study.Case(Ca=1.7, De=2.0, lam=1.0, conf=0.7, phase=2, w=64)
+    p40, p64 = study.case_params(c40), study.case_params(c64)
+    assert (p40.Lx, p40.Ly, p40.Lz) == (study.LX, study.LY, study.W)
+    assert (p64.Lx, p64.Ly, p64.Lz) == (512, 72, 64)
+    assert p64.R == 0.5 * 0.7 * 64
+    assert abs(p64.eta_M - p40.eta_M) < 1e-12 and abs(p64.eta_P - p40.eta_P) < 1e-12
+    # the emulsion time (in steps) grows with W at a fixed wall speed
+    assert abs(study.tau_em(c64) / study.tau_em(c40) - 64 / 40) < 1e-12
