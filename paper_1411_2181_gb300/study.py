@@ -185,6 +185,57 @@ def run_batch(cases: list[Case], device=None, stats: dict | None = None) -> list
     return out
 
 
+def breakup_details(cases: list[Case], device=None, every_tem: float = 0.25, after_tem: float = 3.0) -> list[dict]:
+    """How each case breaks (Sec. 3: binary break-up, or multiple necks and
+    equal daughter droplets under strong confinement): observed every
+    every_tem emulsion times up to T_MAX_TEM, and for after_tem more once it
+    broke.  Per case: the largest neck count before break-up, the break-up
+    time, the fragment count at break-up and the largest one after it."""
+    import torch
+    from . import lbfe
+    ps = [case_params(c) for c in cases]
+    tem = [p.R * p.eta_M / p.sigma for p in ps]
+    every = [max(1, int(round(every_tem * t))) for t in tem]
+    out = [{"case": c.__dict__.copy(), "necks_before": 0, "t_break": None, "fragments_at_break": 0,
+            "fragments_max": 0, "ok": True} for c in cases]
+    end = [int(math.ceil(T_MAX_TEM * t / e)) * e for t, e in zip(tem, every)]
+    stream = torch.cuda.Stream(device)
+    with torch.cuda.stream(stream):
+        s = lbfe.Solver(ps, device=device, stream=stream)
+        s.tune(8, 0, 0)
+        for k, (c, p) in enumerate(zip(cases, ps)):
+            s.init(k, synth.droplet_densities(p.Lx, p.Ly, p.Lz, p.R, p.rho_in, p.rho_out, 1e-4, seed=c.seed))
+        nxt, steps = list(every), 0
+        while True:
+            live = [k for k in range(len(cases)) if out[k]["ok"] and nxt[k] <= end[k]]
+            if not live:
+                break
+            target = min(nxt[k] for k in live)
+            s.step(target - steps)
+            steps = target
+            for k in live:
+                if nxt[k] != steps:
+                    continue
+                nxt[k] += every[k]
+                ob = s.observables(k, raise_on_diverged=False)
+                o = out[k]
+                if ob["flags"]:
+                    o["ok"] = False
+                    continue
+                if o["t_break"] is None:
+                    if ob["broken"]:
+                        o["t_break"] = steps / tem[k]
+                        o["fragments_at_break"] = o["fragments_max"] = ob["fragments"]
+                        end[k] = min(end[k], steps + int(math.ceil(after_tem * tem[k] / every[k])) * every[k])
+                    else:
+                        o["necks_before"] = max(o["necks_before"], ob["necks"])
+                else:
+                    o["fragments_max"] = max(o["fragments_max"], ob["fragments"])
+        torch.cuda.synchronize()
+        s.close()
+    return out
+
+
 DE_TRAIN = (0.0, 0.5, 1.0, 1.5, 2.0)
 
 

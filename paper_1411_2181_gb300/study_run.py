@@ -21,7 +21,9 @@ search   searches Ca_cr for held-out (De, lambda, 2R/W) triples of the
          simulations, batched rounds and wall time, and per triple both
          brackets;
 trend    Ca_cr by bisection against the confinement for Newtonian, droplet-
-         and matrix-viscoelastic droplets (the trends of Figs. 2 and 4).
+         and matrix-viscoelastic droplets (the trends of Figs. 2 and 4);
+breakup  how given cases break: necks before break-up, break-up time and
+         the number of fragments (binary or multiple break-up, Sec. 3).
 """
 from __future__ import annotations
 
@@ -191,6 +193,17 @@ def trend(out=None, lam=1.0, confs=(0.6, 0.7, 0.8), uw=study.UW, ca_max=study.CA
     return rep
 
 
+def breakup(specs, out=None, uw=study.UW, w=study.W):
+    """Break-up details (study.breakup_details) of cases given as
+    (De, lambda, 2R/W, phase, Ca), run as one batch."""
+    cases = [study.Case(Ca=ca, De=de, lam=lam, conf=conf, phase=int(ph), seed=7, uw=uw, w=w)
+             for de, lam, conf, ph, ca in specs]
+    t0 = time.perf_counter()
+    rep = {"W": w, "Uw": uw, "cases": study.breakup_details(cases), "seconds": time.perf_counter() - t0}
+    _emit(rep, out)
+    return rep
+
+
 def _emit(rep, out):
     txt = json.dumps(rep, indent=1)
     print(txt)
@@ -226,6 +239,11 @@ def main(argv=None):
     r.add_argument("--de", type=float, default=2.0, help="Deborah number of the DV and MV droplets")
     r.add_argument("--w", type=int, default=study.W, help="gap W (the box scales with it)")
     r.add_argument("--kinds", default="newtonian,DV,MV")
+    b = sub.add_parser("breakup")
+    b.add_argument("--case", action="append", required=True, help="De,lambda,2R/W,phase,Ca (repeatable)")
+    b.add_argument("--uw", type=float, default=study.UW)
+    b.add_argument("--w", type=int, default=study.W)
+    b.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     if a.cmd == "collect":
         return collect(a.n, a.seed, a.out, mv_ca_from=a.mv_ca_from)
@@ -234,6 +252,8 @@ def main(argv=None):
     if a.cmd == "search":
         info = json.load(open(a.train_info)) if a.train_info else None
         return search(a.params, a.triples, a.out, a.delta, info)
+    if a.cmd == "breakup":
+        return breakup([tuple(float(x) for x in c.split(",")) for c in a.case], a.out, uw=a.uw, w=a.w)
     return trend(a.out, a.lam, uw=a.uw, ca_max=a.ca_max, de=a.de, w=a.w, kinds=tuple(a.kinds.split(",")))
 
 
