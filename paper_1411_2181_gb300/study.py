@@ -190,14 +190,15 @@ def breakup_details(cases: list[Case], device=None, every_tem: float = 0.25, aft
     equal daughter droplets under strong confinement): observed every
     every_tem emulsion times up to T_MAX_TEM, and for after_tem more once it
     broke.  Per case: the largest neck count before break-up, the break-up
-    time, the fragment count at break-up and the largest one after it."""
+    time, the fragment count at break-up and the largest one after it, and
+    the fragment count at every observation from the break-up on."""
     import torch
     from . import lbfe
     ps = [case_params(c) for c in cases]
     tem = [p.R * p.eta_M / p.sigma for p in ps]
     every = [max(1, int(round(every_tem * t))) for t in tem]
     out = [{"case": c.__dict__.copy(), "necks_before": 0, "t_break": None, "fragments_at_break": 0,
-            "fragments_max": 0, "ok": True} for c in cases]
+            "fragments_max": 0, "fragments_after": [], "ok": True} for c in cases]
     end = [int(math.ceil(T_MAX_TEM * t / e)) * e for t, e in zip(tem, every)]
     stream = torch.cuda.Stream(device)
     with torch.cuda.stream(stream):
@@ -226,11 +227,13 @@ def breakup_details(cases: list[Case], device=None, every_tem: float = 0.25, aft
                     if ob["broken"]:
                         o["t_break"] = steps / tem[k]
                         o["fragments_at_break"] = o["fragments_max"] = ob["fragments"]
+                        o["fragments_after"].append(ob["fragments"])
                         end[k] = min(end[k], steps + int(math.ceil(after_tem * tem[k] / every[k])) * every[k])
                     else:
                         o["necks_before"] = max(o["necks_before"], ob["necks"])
                 else:
                     o["fragments_max"] = max(o["fragments_max"], ob["fragments"])
+                    o["fragments_after"].append(ob["fragments"])
         torch.cuda.synchronize()
         s.close()
     return out

@@ -193,13 +193,14 @@ def trend(out=None, lam=1.0, confs=(0.6, 0.7, 0.8), uw=study.UW, ca_max=study.CA
     return rep
 
 
-def breakup(specs, out=None, uw=study.UW, w=study.W):
+def breakup(specs, out=None, uw=study.UW, w=study.W, every_tem=0.25):
     """Break-up details (study.breakup_details) of cases given as
     (De, lambda, 2R/W, phase, Ca), run as one batch."""
     cases = [study.Case(Ca=ca, De=de, lam=lam, conf=conf, phase=int(ph), seed=7, uw=uw, w=w)
              for de, lam, conf, ph, ca in specs]
     t0 = time.perf_counter()
-    rep = {"W": w, "Uw": uw, "cases": study.breakup_details(cases), "seconds": time.perf_counter() - t0}
+    rep = {"W": w, "Uw": uw, "every_tem": every_tem, "cases": study.breakup_details(cases, every_tem=every_tem),
+           "seconds": time.perf_counter() - t0}
     _emit(rep, out)
     return rep
 
@@ -243,6 +244,7 @@ def main(argv=None):
     b.add_argument("--case", action="append", required=True, help="De,lambda,2R/W,phase,Ca (repeatable)")
     b.add_argument("--uw", type=float, default=study.UW)
     b.add_argument("--w", type=int, default=study.W)
+    b.add_argument("--every", type=float, default=0.25, help="observation interval in emulsion times")
     b.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     if a.cmd == "collect":
@@ -253,7 +255,8 @@ def main(argv=None):
         info = json.load(open(a.train_info)) if a.train_info else None
         return search(a.params, a.triples, a.out, a.delta, info)
     if a.cmd == "breakup":
-        return breakup([tuple(float(x) for x in c.split(",")) for c in a.case], a.out, uw=a.uw, w=a.w)
+        return breakup([tuple(float(x) for x in c.split(",")) for c in a.case], a.out, uw=a.uw, w=a.w,
+                       every_tem=a.every)
     return trend(a.out, a.lam, uw=a.uw, ca_max=a.ca_max, de=a.de, w=a.w, kinds=tuple(a.kinds.split(",")))
 
 
