@@ -244,10 +244,12 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload_name: str, precision: int):
+def profiled_traffic(workload_name: str, precision: int, advection: int = 0):
     """DRAM bytes per lattice update of the step from the committed ncu
     summary, if it was taken on the current kernel sources."""
-    fn = os.path.join(ROOT, "profiles", f"step_{workload_name}_{['fp32', 'fp16', 'bf16'][precision]}.md")
+    suffix = "_upwind2" if advection else ""
+    fn = os.path.join(ROOT, "profiles",
+                      f"step_{workload_name}_{['fp32', 'fp16', 'bf16'][precision]}{suffix}.md")
     if not os.path.exists(fn):
         return None, None
     txt = open(fn).read()
@@ -359,8 +361,7 @@ def roofline_record(prec: int, ncell: int, ms_per_step: float, workload_name: st
     peak, peak_kind = measured_peak()
     algo = ALGO_BYTES[prec]
     achieved = algo * ncell / (ms_per_step / 1e3) / 1e9
-    # the committed summaries are of the default (first-order) step kernel
-    traffic_per_lup, prof_file = (profiled_traffic(workload_name, prec) if advection == 0 else (None, None))
+    traffic_per_lup, prof_file = profiled_traffic(workload_name, prec, advection)
     return {"bound": "hbm", "kernel": "k_fused (whole time step in one kernel)",
             "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "algorithmic_bytes_per_lup": algo,
