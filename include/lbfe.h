@@ -60,7 +60,12 @@ typedef enum {
     LBFE_FP32 = 0,            /* populations stored in FP32 */
     LBFE_FP16_OFFSET = 1,     /* stored as FP16 offsets f - w_i rho_s', FP32 compute */
     LBFE_BF16_OFFSET = 2      /* stored as BF16 offsets f - w_i rho_s', FP32 compute; rho_s' is
-                                 the cell's own density of the previous step, kept in FP32 */
+                                 the cell's own density of the previous step, kept in FP32.
+                                 The step's stores round stochastically, with random bits
+                                 drawn from the destination cell, the direction and the
+                                 instance's step count (deterministic: a run, a batch member
+                                 and a run resumed by lbfe_load give the same bits); FP16
+                                 rounds to nearest */
 } lbfe_precision;
 
 typedef enum {

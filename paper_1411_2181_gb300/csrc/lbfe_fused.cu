@@ -101,6 +101,8 @@ k_fused(const __grid_constant__ StepArgs A) {
         const float *__restrict__ Cin = I.Cin;
         float *__restrict__ Cout = I.Cout;
         const float Uw = I.Uw;
+        // the instance's step count: the seed of the BF16 stochastic rounding
+        const unsigned seed = (Store<T>::sround && I.step_ctr) ? __ldcg(I.step_ctr) : 0u;
 
         __syncthreads();  // previous item done with the row/column tables
         if (t < RY) s_rows[t] = (u32)(wrapg(y0 + t, Ly) * Lx);
@@ -305,6 +307,7 @@ k_fused(const __grid_constant__ StepArgs A) {
                     Po.own = make_float2(rAo, rBo);
                     Po.track = I.dens_out != nullptr;
                     Po.r0 = make_float2(I.rho0A, I.rho0B);
+                    Po.seed = seed;
                     const float2 F2[3] = {make_float2(FA[0], FB[0]), make_float2(FA[1], FB[1]),
                                           make_float2(FA[2], FB[2])};
                     if (!kSplitWalls || bottom || top)
@@ -335,7 +338,7 @@ k_fused(const __grid_constant__ StepArgs A) {
         slot ^= 1;
     }
 
-    if (t == 0 && A.total_items > (int)gridDim.x) release_work_counters(A.work);
+    if (t == 0) finish_launch(A);
     if (expired) {
         // issuer: the copy whose wait expired may still be in flight (no
         // later one was issued); wait for its phase once more, bounded,
@@ -375,6 +378,7 @@ void fill_inst(StepInst &d, const InstDev &I, const PopMaps *maps, const StepMap
     d.dens_in = I.dens[cur ^ 1];
     d.dens_out = I.dens[cur];
     d.status = I.status;
+    d.step_ctr = I.step_ctr;
     d.G = I.G;
     d.Uw = I.Uw;
     d.nu_A = I.nu_A;

@@ -278,7 +278,26 @@ struct PairPush {
     float2 ownA, ownB;       // the pair's densities
     bool track;
     float r0[2];
+    unsigned seed;           // the instance's step count (stochastic rounding)
 };
+
+// Component s of population `dir` into cells c0 and c1 (at p0 and p1,
+// adjacent when `adjacent`): vector stores rounding to nearest, or for
+// BF16 one stochastically rounded store per cell with the random bits the
+// one-cell kernel draws for that cell, direction and step.
+template <typename T>
+__device__ __forceinline__ void store_pair(T *p0, T *p1, float2 v, bool adjacent, u32 c0, u32 c1, int dir, int s,
+                                           unsigned seed) {
+    if (Store<T>::sround) {
+        Store<T>::st_sr(p0, v.x, sround_bits(c0, dir, seed) >> (16 * s));
+        Store<T>::st_sr(p1, v.y, sround_bits(c1, dir, seed) >> (16 * s));
+    } else if (adjacent) {
+        Pair<T>::stg(p0, v);
+    } else {
+        Store<T>::st(p0, v.x);
+        Store<T>::st(p1, v.y);
+    }
+}
 
 template <typename T>
 __device__ __forceinline__ float2 pair_dest_offset(const PairPush &P, int s, int d, bool wall) {
@@ -297,18 +316,15 @@ __device__ __forceinline__ void push2(T *__restrict__ fdst, u32 S, int s, int d,
         v = fma2(bc(-6.f * wq(d) * (float)cx(d) * (cz(d) < 0 ? -Uw : Uw)), rs, v);
         if (Store<T>::offset) v = fma2(bc(-wq(d)), pair_dest_offset<T>(P, s, d, true), v);
         const u32 dst = P.q_plane + P.row[1] + P.col0[1];
-        Pair<T>::stg(fdst + (u32)((s * Q + opp(d)) * S + dst), v);
+        T *p = fdst + (u32)((s * Q + opp(d)) * S + dst);
+        store_pair<T>(p, p + 1, v, true, dst, dst + 1, opp(d), s, P.seed);
         return;
     }
     if (Store<T>::offset) v = fma2(bc(-wq(d)), pair_dest_offset<T>(P, s, d, false), v);
     const u32 plane = P.q_plane + (u32)(cz(d) * P.LxLy) + P.row[cy(d) + 1];
     T *base = fdst + (u32)((s * Q + d) * S);
-    if (cx(d) == 0) {
-        Pair<T>::stg(base + (plane + P.col0[1]), v);
-    } else {
-        Store<T>::st(base + (plane + P.col0[cx(d) + 1]), v.x);
-        Store<T>::st(base + (plane + P.col1[cx(d) + 1]), v.y);
-    }
+    const u32 c0 = plane + P.col0[cx(d) + 1], c1 = plane + P.col1[cx(d) + 1];
+    store_pair<T>(base + c0, base + c1, v, cx(d) == 0, c0, c1, d, s, P.seed);
 }
 
 // BGK + Guo collision of one component of the pair and push streaming (the
@@ -328,7 +344,9 @@ __device__ __forceinline__ void collide_push2(const float2 *fv, T *__restrict__ 
             const float2 o = P.track ? (s == 0 ? P.ownA : P.ownB) : bc(P.r0[s]);
             v = fma2(bc(-wq(0)), o, v);
         }
-        Pair<T>::stg(fdst + (u32)(s * Q * S + P.q_plane + P.row[1] + P.col0[1]), v);
+        const u32 c0 = P.q_plane + P.row[1] + P.col0[1];
+        T *p = fdst + (u32)(s * Q * S + c0);
+        store_pair<T>(p, p + 1, v, true, c0, c0 + 1, 0, s, P.seed);
     }
     float2 Ew[2], a1w[2], b1w[2], a2w[2], b2w[2];
 #pragma unroll
@@ -448,6 +466,8 @@ __global__ void __launch_bounds__(PNT, 1) k_fused_pair(const __grid_constant__ S
         Pp.LxLy = LxLy;
         Pp.idx = idx_in;
         Pp.track = I.dens_out != nullptr;
+        // the instance's step count: the seed of the BF16 stochastic rounding
+        Pp.seed = (Store<T>::sround && I.step_ctr) ? __ldcg(I.step_ctr) : 0u;
         Pp.r0[0] = I.rho0A;
         Pp.r0[1] = I.rho0B;
         // this thread's halo pair
@@ -590,7 +610,7 @@ __global__ void __launch_bounds__(PNT, 1) k_fused_pair(const __grid_constant__ S
         slot ^= 1;
     }
 
-    if (t == 0 && A.total_items > (int)gridDim.x) release_work_counters(A.work);
+    if (t == 0) finish_launch(A);
     if (expired) {
         // thread 0: the copy whose wait expired may still be in flight: wait
         // for its phase once more, bounded, before the shared memory is

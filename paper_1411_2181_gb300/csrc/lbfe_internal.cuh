@@ -41,27 +41,56 @@ __host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i 
 // most of the SM's L1/shared capacity as shared memory, and their few
 // ordinary loads are throttled when they compete for the small L1.
 template <typename T> struct Store;
+// st_sr(p, v, r): the store of a time step's populations.  FP32 and FP16
+// round to nearest (r unused).  BF16 rounds stochastically: the 16 random
+// bits r are added to the FP32 bit pattern below the BF16 mantissa and the
+// sum is truncated, so that v rounds up with probability equal to its
+// distance from the lower BF16 neighbour in units of the spacing.
+// Rounding to nearest repeats the same error in a near-steady state step
+// after step; the random bits make the errors average out.
 template <> struct Store<float> {
     static constexpr bool offset = false;
+    static constexpr bool sround = false;
     static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
     static __device__ __forceinline__ float ld_l2(const float *p) { return __ldcg(p); }
     static __device__ __forceinline__ float ld_plain(const float *p) { return *p; }
     static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+    static __device__ __forceinline__ void st_sr(float *p, float v, unsigned) { *p = v; }
 };
 template <> struct Store<__half> {
     static constexpr bool offset = true;
+    static constexpr bool sround = false;
     static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ float ld_l2(const __half *p) { return __half2float(__ldcg(p)); }
     static __device__ __forceinline__ float ld_plain(const __half *p) { return __half2float(*p); }
     static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ void st_sr(__half *p, float v, unsigned) { *p = __float2half_rn(v); }
 };
 template <> struct Store<__nv_bfloat16> {
     static constexpr bool offset = true;
+    static constexpr bool sround = true;
     static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
     static __device__ __forceinline__ float ld_l2(const __nv_bfloat16 *p) { return __bfloat162float(__ldcg(p)); }
     static __device__ __forceinline__ float ld_plain(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ void st_sr(__nv_bfloat16 *p, float v, unsigned r16) {
+        *reinterpret_cast<unsigned short *>(p) = (unsigned short)((__float_as_uint(v) + (r16 & 0xFFFFu)) >> 16);
+    }
 };
+
+// Random bits of the stochastic rounding: 32 bits per (destination cell,
+// direction, step), the low half for component A and the high half for B;
+// the integer hash is "lowbias32" (C. Wellons, hash-prospector), applied to
+// the cell and direction mixed with the step by a Weyl constant.
+__device__ __forceinline__ unsigned sround_bits(unsigned cell, int dir, unsigned step) {
+    unsigned x = (cell * 19u + (unsigned)dir) ^ (step * 0x9E3779B9u);
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
 
 // Device descriptor of one instance (all pointers into the caller's block).
 struct InstDev {
@@ -83,6 +112,7 @@ struct InstDev {
                                      // the state in f[c] is stored relative to w_i * dens[c ^ 1]
     int ntx, nty, nzc, zc;           // fused kernel: column tiles in x, y; z-chunks and their depth
     unsigned *status;                // this instance's status word (may be null)
+    unsigned *step_ctr;              // time steps taken (the seed of the BF16 stochastic rounding)
 };
 
 // Raise a status flag for the whole launch and, when present, for instance I.

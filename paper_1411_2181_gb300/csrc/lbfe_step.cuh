@@ -81,6 +81,7 @@ struct StepInst {
     const float2 *dens_in;         // offsets of the state read (reduced forms with tracking, else null)
     float2 *dens_out;              // offsets of the state written
     unsigned *status;              // per-instance status word (may be null)
+    unsigned *step_ctr;            // time steps taken (BF16 stochastic rounding seed; may be null)
     float G, Uw, nu_A, nu_B, pi_coef, L2, inv_tauP, gx, gy, gz, rho0A, rho0B;
     u32 S, LxLy;                   // field stride, cells per plane
     unsigned short Lx, Ly, Lz, ntx, nty, zc;
@@ -733,6 +734,7 @@ struct PushOffsets {
     float2 own;              // the pushing cell's densities
     bool track;
     float2 r0;               // constant offsets
+    unsigned seed;           // the instance's step count (stochastic rounding)
 };
 
 template <int RX>
@@ -761,8 +763,9 @@ __device__ __forceinline__ void push_ab(T *__restrict__ fdst, u32 S, int d, floa
         wall = true;
     }
     if (Store<T>::offset) v = fma2(bc(-wq(d)), push_offset<RX>(P, d, wall), v);
-    Store<T>::st(fdst + (u32)(dir * S + dst), v.x);
-    Store<T>::st(fdst + (u32)((Q + dir) * S + dst), v.y);
+    const unsigned r = Store<T>::sround ? sround_bits(dst, dir, P.seed) : 0u;
+    Store<T>::st_sr(fdst + (u32)(dir * S + dst), v.x, r);
+    Store<T>::st_sr(fdst + (u32)((Q + dir) * S + dst), v.y, r >> 16);
 }
 
 // BGK + Guo collision of both components of one cell, on packed FP32 (lane
@@ -790,8 +793,9 @@ __device__ __forceinline__ void collide_push_ab(const float2 *fv, T *__restrict_
     {
         float2 v = fma2(omc2, fv[0], mul2(bc(wq(0)), E));
         if (Store<T>::offset) v = fma2(bc(-wq(0)), P.track ? P.own : P.r0, v);
-        Store<T>::st(fdst + n, v.x);
-        Store<T>::st(fdst + (u32)(Q * S + n), v.y);
+        const unsigned r = Store<T>::sround ? sround_bits(n, 0, P.seed) : 0u;
+        Store<T>::st_sr(fdst + n, v.x, r);
+        Store<T>::st_sr(fdst + (u32)(Q * S + n), v.y, r >> 16);
     }
     // weight classes: faces (i = 1..6) and edges (i = 7..18)
     float2 Ew[2], a1w[2], b1w[2], a2w[2], b2w[2];
@@ -836,12 +840,16 @@ __device__ __forceinline__ void collide_push_ab(const float2 *fv, T *__restrict_
 // work[0] before its arrival on work[1], so the last arriver's reset comes
 // after every other block's final fetch; the reset itself is atomic and
 // fenced before the kernel ends.
-__device__ __forceinline__ void release_work_counters(unsigned *work) {
+// The last block also advances every instance's step count (read by all
+// blocks at the start of their items, so only once every block is done).
+__device__ __forceinline__ void finish_launch(const StepArgs &A) {
     __threadfence();
-    if (atomicAdd(work + 1, 1u) == gridDim.x - 1) {
+    if (atomicAdd(A.work + 1, 1u) == gridDim.x - 1) {
         __threadfence();
-        atomicExch(work, 0u);
-        atomicExch(work + 1, 0u);
+        for (int k = 0; k < A.n; ++k)
+            if (A.inst[k].step_ctr) atomicAdd(A.inst[k].step_ctr, 1u);
+        atomicExch(A.work, 0u);
+        atomicExch(A.work + 1, 0u);
         __threadfence();
     }
 }
