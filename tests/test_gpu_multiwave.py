@@ -75,11 +75,12 @@ def test_config2_multiwave_matches_oracle(L, cfg2_oracle, kernel, tile_y):
 
 
 @pytest.mark.parametrize("kernel,tile_y", SHAPES)
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_config2_multiwave_equals_single_wave(L, cfg2_oracle, kernel, tile_y, prec):
     """The same steps with every item in the first wave (one z-chunk per
     column tile) and with 8-plane chunks on several waves give identical
-    fields, in FP32 and FP16 storage, over single steps and graph replays."""
+    fields, in FP32, FP16 and BF16 storage (stochastic rounding), over
+    single steps and graph replays."""
     p, rho, f0, C0, _ = cfg2_oracle
     p = replace(p, precision=prec)
     one = _solver(L, p, rho, f0, C0, tile_y, p.Lz, kernel)
@@ -148,3 +149,30 @@ def test_uneven_batch_multiwave_equals_solo_runs(L, kernel, tile_y):
     orc.step(sum(schedule))
     assert norm_err(batch.get_field(k, L.FIELD_F), orc.f, 2) < 5 * TOL_FEW
     assert tensor_err(batch.get_field(k, L.FIELD_C), orc.C) < 5 * TOL_FEW
+
+
+@pytest.mark.parametrize("kernel,tile_y", [(0, 8), (1, 16)])
+def test_bf16_step_counts_are_per_instance(L, kernel, tile_y):
+    """BF16 storage draws its rounding bits from each instance's own step
+    count: a batch member re-initialised in the middle of a run restarts
+    its count and equals a fresh solo run, the others equal solo runs of
+    the whole schedule, bit for bit."""
+    ps, rhos = _uneven_batch(L, n=3, seed=21)
+    ps = [replace(p, Lx=p.Lx + (p.Lx % 2), precision=2) for p in ps]
+    rhos = [synth.droplet_densities(p.Lx, p.Ly, p.Lz, p.R, seed=200 + k) for k, p in enumerate(ps)]
+    batch = L.Solver(ps)
+    batch.tune(tile_y, 0, kernel)
+    for k, r in enumerate(rhos):
+        batch.init(k, r)
+    batch.step(3)
+    batch.init(1, rhos[1])
+    batch.step(1)
+    batch.step(4)
+    assert batch.check() == L.OK
+    for k, (p, r) in enumerate(zip(ps, rhos)):
+        solo = L.Solver(p)
+        solo.tune(tile_y, 0, kernel)
+        solo.init(0, r)
+        solo.step(5 if k == 1 else 8)
+        assert np.array_equal(batch.get_field(k, L.FIELD_F), solo.get_field(0, L.FIELD_F)), k
+        solo.close()

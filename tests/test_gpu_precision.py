@@ -59,7 +59,7 @@ def test_fp32_observables_match_oracle(runs, oracle_run):
         assert ro["volume"] == 0 or abs(g["volume"] / ro["volume"] - 1) < 1e-3
 
 
-@pytest.mark.parametrize("prec,tol_D,tol_theta,tol_mass", [(1, 1e-3, 0.05, 1e-4), (2, 5e-3, 0.5, 1e-3)])
+@pytest.mark.parametrize("prec,tol_D,tol_theta,tol_mass", [(1, 1e-3, 0.05, 1e-4), (2, 1e-3, 0.05, 1e-4)])
 def test_reduced_storage_against_oracle(runs, oracle_run, prec, tol_D, tol_theta, tol_mass):
     """The reduced forms against the FP64 oracle over 3000 steps: deformation,
     orientation and each component's mass (relative to the oracle's, which
@@ -74,7 +74,7 @@ def test_reduced_storage_against_oracle(runs, oracle_run, prec, tol_D, tol_theta
     assert dD < tol_D and dth < tol_theta and dm < tol_mass
 
 
-@pytest.mark.parametrize("prec,tol_D,tol_theta,tol_mass", [(1, 1e-3, 0.05, 1e-4), (2, 5e-3, 0.5, 1e-3)])
+@pytest.mark.parametrize("prec,tol_D,tol_theta,tol_mass", [(1, 1e-3, 0.05, 1e-4), (2, 1e-3, 0.05, 1e-4)])
 def test_reduced_storage_errors(runs, prec, tol_D, tol_theta, tol_mass):
     ref, red = runs[0], runs[prec]
     dD = max(abs(a["D"] - b["D"]) for a, b in zip(ref, red))
@@ -107,10 +107,12 @@ def test_reduced_storage_launch_shapes_agree(L, prec):
 
 def test_full_lattice_reduced_storage_10k_steps(L):
     """The full 256 x 128 x 64 lattice of the workload over its 10^4 steps
-    (beyond the oracle's reach in the suite): FP16 storage keeps the
+    (beyond the oracle's reach in the suite): both reduced forms keep the
     deformation within 1e-3 of FP32 storage, the bound the reduced form is
-    held to; BF16 (8-bit mantissa) is held to the looser bounds its measured
-    errors set (max |dD| 8.3e-3, |dtheta| 0.49 deg, relative mass 1.6e-2)."""
+    held to.  BF16 rounds stochastically; its measured errors (max |dD|
+    4.8e-5, |dtheta| 0.012 deg, relative mass 1.4e-5) are held to 1e-3,
+    0.05 deg and 2e-4 (with rounding to nearest they were 8.3e-3, 0.49 deg
+    and 1.6e-2)."""
     p, rho, _ = configs.config3()
     steps, every = 10000, 500
     traj = {}
@@ -124,7 +126,7 @@ def test_full_lattice_reduced_storage_10k_steps(L):
         assert s.check() == L.OK
         traj[prec] = out
         s.close()
-    for prec, tol_D, tol_theta, tol_mass in ((1, 1e-3, 0.1, 1e-3), (2, 2e-2, 1.0, 3e-2)):
+    for prec, tol_D, tol_theta, tol_mass in ((1, 1e-3, 0.1, 1e-3), (2, 1e-3, 0.05, 2e-4)):
         ref, red = traj[0], traj[prec]
         dD = max(abs(a["D"] - b["D"]) for a, b in zip(ref, red))
         dth = max(abs(a["theta_deg"] - b["theta_deg"]) for a, b in zip(ref[1:], red[1:]))
