@@ -30,6 +30,9 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--every", type=int, default=500)
     ap.add_argument("--full-steps", type=int, default=0)
+    ap.add_argument("--mass-drift", action="store_true",
+                    help="component masses of the reduced forms against FP32 storage every 1000 steps "
+                         "over 10^4 steps on 64 x 64, 128 x 64 and 256 x 128 cross-sections")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     from paper_1411_2181_gb300 import build
@@ -39,6 +42,8 @@ def main(argv=None):
         rep = crop_against_oracle(a.steps, a.every)
     if a.full_steps > 0:
         rep["full"] = full_lattice(a.full_steps, a.every)
+    if a.mass_drift:
+        rep["mass_drift"] = mass_drift()
     txt = json.dumps(rep, indent=1)
     print(txt)
     if a.out:
@@ -119,6 +124,42 @@ def full_lattice(steps: int, every: int) -> dict:
                                              np.array(y["mass"])).max()) for x, y in zip(g, ref)),
             "final_D": g[-1]["D"], "final_theta_deg": g[-1]["theta_deg"]}
     return rep
+
+
+def mass_drift() -> dict:
+    """The reduced forms' component masses against FP32 storage every 1000
+    steps over 10^4 steps, for the same droplet and gap on three x-y
+    cross-sections (absolute differences per component, and relative ones
+    at the end)."""
+    from dataclasses import replace
+
+    import numpy as np
+
+    from paper_1411_2181_gb300 import configs, lbfe, synth
+    out = {}
+    for Lx, Ly in ((64, 64), (128, 64), (256, 128)):
+        p0, _, _ = configs.config3()
+        p0 = replace(p0, Lx=Lx, Ly=Ly)
+        rho = synth.droplet_densities(Lx, Ly, 64, 22.0, configs.RHO_IN, configs.RHO_OUT, configs.NOISE, seed=3)
+        tr = {}
+        for prec in (0, 1, 2):
+            s = lbfe.Solver(replace(p0, precision=prec))
+            s.init(0, rho)
+            m = [s.observables(0)["mass"]]
+            for _ in range(10):
+                s.step(1000)
+                m.append(s.observables(0)["mass"])
+            tr[prec] = np.array(m)
+            s.close()
+        rep = {}
+        for prec in (1, 2):
+            d = tr[prec] - tr[0]
+            rep[["", "fp16", "bf16"][prec]] = {
+                "abs_A": d[:, 0].tolist(), "abs_B": d[:, 1].tolist(),
+                "rel_A_end": float(d[-1, 0] / tr[0][-1, 0]), "rel_B_end": float(d[-1, 1] / tr[0][-1, 1])}
+        rep["mass_fp32"] = tr[0][[0, -1]].tolist()
+        out[f"{Lx}x{Ly}"] = rep
+    return out
 
 
 if __name__ == "__main__":
