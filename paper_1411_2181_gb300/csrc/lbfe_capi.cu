@@ -108,8 +108,9 @@ Layout plan(const lbfe_params *p, int n) {
     L.inst_off = take(sizeof(InstDev) * (size_t)n);
     L.tile_off = take(sizeof(int) * (size_t)(n + 1));
     L.item_off = take(sizeof(int) * (size_t)(n + 1));
-    // launch word, work counters, then one status word and one step count per instance
-    L.status_off = take(sizeof(unsigned) * (4 + 2 * (size_t)n));
+    // launch word, work counters, then one status word per instance and
+    // two step-count words per instance (by ping-pong parity)
+    L.status_off = take(sizeof(unsigned) * (4 + 3 * (size_t)n));
     L.mass_off = take(sizeof(double) * 2);
     L.maps_off = take(sizeof(lbfe::StepMaps) * 2 * (size_t)n);   // TMA maps, [instance][parity]
     const size_t eb = elem_bytes(p[0].precision);
@@ -369,7 +370,7 @@ lbfe_status lbfe_create(lbfe_handle **hp, const lbfe_params *p, int n, void *dev
         I.F = scr + 8 * I.S;
         I.prof = (unsigned long long *)(h->base + L.prof_off[k]);
         I.status = h->status + 4 + k;
-        I.step_ctr = h->status + 4 + n + k;
+        I.step_ctr = h->status + 4 + n + 2 * k;
         I.mpart = (double *)(h->base + L.mpart_off[k]);
         I.G = (float)p[k].G;
         I.Uw = (float)p[k].Uw;
@@ -392,7 +393,7 @@ lbfe_status lbfe_create(lbfe_handle **hp, const lbfe_params *p, int n, void *dev
     h->total_tiles = toff[n];
     cudaError_t e = cudaMemcpyAsync(h->inst_dev, h->inst.data(), sizeof(InstDev) * n, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->tile_off, toff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(unsigned) * (4 + 2 * (size_t)n), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(unsigned) * (4 + 3 * (size_t)n), h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     const size_t smem = sizeof(unsigned long long) * 6 * (size_t)maxLx;
     if (e == cudaSuccess && smem > 48 * 1024) e = lbfe::obs_set_smem_limit(smem);
@@ -424,7 +425,7 @@ lbfe_status lbfe_init(lbfe_handle *h, int k, const double *rho_init) {
     CK(cudaMemcpyAsync(stage, rho_init, sizeof(double) * 2 * (size_t)I.N, cudaMemcpyHostToDevice, h->stream));
     CK(lbfe::launch_init(h->ctx(), k, stage, h->cur));
     CK(cudaMemsetAsync(I.status, 0, sizeof(unsigned), h->stream));
-    CK(cudaMemsetAsync(I.step_ctr, 0, sizeof(unsigned), h->stream));
+    CK(cudaMemsetAsync(I.step_ctr, 0, 2 * sizeof(unsigned), h->stream));
     CK(cudaStreamSynchronize(h->stream));
     h->steps[k] = 0;
     h->ready[k] = 1;
@@ -795,7 +796,7 @@ lbfe_status lbfe_load(lbfe_handle *h, int k, const char *path) {
     // the step count seeds the BF16 stochastic rounding: a resumed run
     // continues with the random bits of an uninterrupted one
     const unsigned step_ctr = (unsigned)hd.steps;
-    CK(cudaMemcpyAsync(I.step_ctr, &step_ctr, sizeof step_ctr, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(I.step_ctr + h->cur, &step_ctr, sizeof step_ctr, cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     h->steps[k] = hd.steps;
     h->ready[k] = 1;

@@ -102,7 +102,7 @@ k_fused(const __grid_constant__ StepArgs A) {
         float *__restrict__ Cout = I.Cout;
         const float Uw = I.Uw;
         // the instance's step count: the seed of the BF16 stochastic rounding
-        const unsigned seed = (Store<T>::sround && I.step_ctr) ? __ldcg(I.step_ctr) : 0u;
+        const unsigned seed = step_seed<Store<T>::sround>(A, I, k, item, t);
 
         __syncthreads();  // previous item done with the row/column tables
         if (t < RY) s_rows[t] = (u32)(wrapg(y0 + t, Ly) * Lx);
@@ -338,7 +338,7 @@ k_fused(const __grid_constant__ StepArgs A) {
         slot ^= 1;
     }
 
-    if (t == 0) finish_launch(A);
+    if (t == 0 && A.total_items > (int)gridDim.x) release_work_counters(A.work);
     if (expired) {
         // issuer: the copy whose wait expired may still be in flight (no
         // later one was issued); wait for its phase once more, bounded,
@@ -379,6 +379,7 @@ void fill_inst(StepInst &d, const InstDev &I, const PopMaps *maps, const StepMap
     d.dens_out = I.dens[cur];
     d.status = I.status;
     d.step_ctr = I.step_ctr;
+    d.parity = (unsigned char)cur;
     d.G = I.G;
     d.Uw = I.Uw;
     d.nu_A = I.nu_A;

@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(PNT, 1) k_fused_pair(const __grid_constant__ S
         Pp.idx = idx_in;
         Pp.track = I.dens_out != nullptr;
         // the instance's step count: the seed of the BF16 stochastic rounding
-        Pp.seed = (Store<T>::sround && I.step_ctr) ? __ldcg(I.step_ctr) : 0u;
+        Pp.seed = step_seed<Store<T>::sround>(A, I, P.k, item, t);
         Pp.r0[0] = I.rho0A;
         Pp.r0[1] = I.rho0B;
         // this thread's halo pair
@@ -610,7 +610,7 @@ __global__ void __launch_bounds__(PNT, 1) k_fused_pair(const __grid_constant__ S
         slot ^= 1;
     }
 
-    if (t == 0) finish_launch(A);
+    if (t == 0 && A.total_items > (int)gridDim.x) release_work_counters(A.work);
     if (expired) {
         // thread 0: the copy whose wait expired may still be in flight: wait
         // for its phase once more, bounded, before the shared memory is

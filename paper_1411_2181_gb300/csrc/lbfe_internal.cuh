@@ -112,7 +112,7 @@ struct InstDev {
                                      // the state in f[c] is stored relative to w_i * dens[c ^ 1]
     int ntx, nty, nzc, zc;           // fused kernel: column tiles in x, y; z-chunks and their depth
     unsigned *status;                // this instance's status word (may be null)
-    unsigned *step_ctr;              // time steps taken (the seed of the BF16 stochastic rounding)
+    unsigned *step_ctr;              // time steps taken, [2] by ping-pong parity (BF16 rounding seed)
 };
 
 // Raise a status flag for the whole launch and, when present, for instance I.

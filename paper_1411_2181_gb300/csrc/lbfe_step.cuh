@@ -81,12 +81,13 @@ struct StepInst {
     const float2 *dens_in;         // offsets of the state read (reduced forms with tracking, else null)
     float2 *dens_out;              // offsets of the state written
     unsigned *status;              // per-instance status word (may be null)
-    unsigned *step_ctr;            // time steps taken (BF16 stochastic rounding seed; may be null)
+    unsigned *step_ctr;            // time steps taken, two words by parity (BF16 rounding seed; may be null)
     float G, Uw, nu_A, nu_B, pi_coef, L2, inv_tauP, gx, gy, gz, rho0A, rho0B;
     u32 S, LxLy;                   // field stride, cells per plane
     unsigned short Lx, Ly, Lz, ntx, nty, zc;
     signed char visc_comp;         // 0 (A), 1 (B), -1 Newtonian
     signed char tma;               // populations (and C) by TMA
+    unsigned char parity;          // ping-pong parity of the state read: step_ctr[parity] is this step's count
 };
 static_assert(sizeof(StepInst) <= 144, "compact launch descriptor");
 
@@ -840,18 +841,27 @@ __device__ __forceinline__ void collide_push_ab(const float2 *fv, T *__restrict_
 // work[0] before its arrival on work[1], so the last arriver's reset comes
 // after every other block's final fetch; the reset itself is atomic and
 // fenced before the kernel ends.
-// The last block also advances every instance's step count (read by all
-// blocks at the start of their items, so only once every block is done).
-__device__ __forceinline__ void finish_launch(const StepArgs &A) {
+__device__ __forceinline__ void release_work_counters(unsigned *work) {
     __threadfence();
-    if (atomicAdd(A.work + 1, 1u) == gridDim.x - 1) {
+    if (atomicAdd(work + 1, 1u) == gridDim.x - 1) {
         __threadfence();
-        for (int k = 0; k < A.n; ++k)
-            if (A.inst[k].step_ctr) atomicAdd(A.inst[k].step_ctr, 1u);
-        atomicExch(A.work, 0u);
-        atomicExch(A.work + 1, 0u);
+        atomicExch(work, 0u);
+        atomicExch(work + 1, 0u);
         __threadfence();
     }
+}
+
+// The step count that seeds the BF16 stochastic rounding of instance k's
+// stores in this launch: step_ctr[parity].  The block that takes the
+// instance's first work item also writes step_ctr[parity ^ 1], the count of
+// the next launch, which no block of this launch reads (so no ordering
+// between the blocks is needed).  Other storage forms read nothing.
+template <bool SROUND>
+__device__ __forceinline__ unsigned step_seed(const StepArgs &A, const StepInst &I, int k, int item, int t) {
+    if (!SROUND || !I.step_ctr) return 0u;
+    const unsigned s = __ldcg(I.step_ctr + I.parity);
+    if (t == 0 && item == A.item_off[k]) I.step_ctr[I.parity ^ 1] = s + 1u;
+    return s;
 }
 
 // Position of work item `item`: instance, column tile and z-chunk.
